@@ -1,0 +1,66 @@
+"""Plant plausible mistakes in copies of the oracle (on the CPU) and check that
+the pins catch every one: each mutant must fail at least one pin."""
+import os
+import subprocess
+
+import pytest
+
+from oracle import oracle as O
+from oracle import build_oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(build_oracle.__file__), "oracle.c")
+
+MUTANTS = {
+    "sqrt_term_sign": ("F = P->k * delta - P->gamma", "F = P->k * delta + P->gamma"),
+    "rbar_formula": ("double rbar = (ri * rj) / (ri + rj);", "double rbar = (ri + rj) / 2.0;"),
+    "cutoff_not_strict": ("if (!(d2 < R2)) continue;", "if (!(d2 <= R2)) continue;"),
+    "accumulate_sign": ("a->fx = a->fx + sc * ddx;", "a->fx = a->fx - sc * ddx;"),
+    "transposed_difference": ("double ddx = xi - st->x[j]", "double ddx = st->x[j] - xi"),
+    "morton_axes_swapped": ("c |= ((y >> b) & 1ULL) << (3 * b + 1);", "c |= ((y >> b) & 1ULL) << (3 * b + 2);"),
+    "no_grid_margin": ("g->lo[d] = floor(mn[d] / P->L) * P->L - P->L;", "g->lo[d] = floor(mn[d] / P->L) * P->L;"),
+    "static_two_contacts": ("st->nz[i] > 1", "st->nz[i] > 2"),
+    "static_ignores_old_position": ("dirty[ndirty++] = G.base[s] + box_linear(g, ox, oy, oz);", "(void)0;"),
+    "cbrt_too_few_steps": ("it < 6", "it < 2"),
+    "philox_weyl_constant": ("W0 = 0x9E3779B97F4A7C15ULL", "W0 = 0x9E3779B97F4A7C17ULL"),
+    "daughter_uid_offset": ("st->next_uid + (uint64_t)rank;", "st->next_uid + (uint64_t)rank + 1;"),
+    "mother_volume": ("double v1 = (v * rho) / (1.0 + rho);", "double v1 = v / (1.0 + rho);"),
+    "clamp_missing": ("if (dn > P->dmax) {", "if (dn > 1e300) {"),
+}
+
+
+def _checks():
+    c = []
+    for row in pins._pair_lines():
+        c.append(lambda row=row: pins.test_two_sphere_hand_worked(*row))
+    for kind in ("uniform", "lattice_ties", "clustered"):
+        c.append(lambda kind=kind: pins.test_grid_neighbors_equal_brute_force(kind))
+    for key, ctr in [((5, 7), (0, 0, 0, 0)), ((2**64 - 1, 123), (2**64 - 1, 3, 9, 1))]:
+        c.append(lambda key=key, ctr=ctr: pins.test_philox_matches_numpy_bit_generator(key, ctr))
+    for dims in [(5, 2, 7), (3, 5)]:
+        c.append(lambda dims=dims: pins.test_morton_offsets_against_brute_force(dims))
+    for name in dir(pins):
+        f = getattr(pins, name)
+        if name.startswith("test_") and callable(f) and f.__code__.co_argcount == 0:
+            c.append(f)
+    return c
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_planted_mistake(name, tmp_path):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, "mutation site not unique: %s" % name
+    mpath = tmp_path / "oracle_mutant.c"
+    mpath.write_text(src.replace(old, new))
+    lib = tmp_path / "liboracle_mutant.so"
+    subprocess.run([os.environ.get("CC", "cc")] + [f for f in build_oracle.CFLAGS if f != "-Wall"]
+                   + [str(mpath), "-o", str(lib), "-lm"], check=True)
+    failures = 0
+    with O.use_library(str(lib)):
+        for chk in _checks():
+            try:
+                chk()
+            except Exception:
+                failures += 1
+    assert failures > 0, "mutant %s survived every pin" % name
