@@ -1,0 +1,367 @@
+#!/usr/bin/env python3
+"""Benchmark: agent-updates/s of the mechanical-interaction iteration on one
+GB300, on the 10M-agent Gaussian-blob workload in the FP32-force form (the
+plain FP64 form is timed beside it), with the roofline of the dominant kernel
+and the FP64 CPU oracle timed on a bounded same-density sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank advances its own
+replica of the workload (weak scaling, no data-path collective); the timed
+region is bracketed by a barrier and the slowest rank's time is reported.
+"""
+import argparse
+import ctypes as C
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "agent-updates/s per mechanical step, FP32-force vs plain FP64 form; % HBM peak"
+UNIT = "agent-updates/s"
+SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
+# algorithmic FP32 work of the force kernel: 8 flops per candidate pair
+# (3 differences, 3 products, 2 sums for d^2) and 20 per contact (radius sum
+# and square, inverse root and distance, overlap, reduced radius, the two force
+# terms and their difference, the scale and three fused accumulations)
+FLOPS_PER_CANDIDATE, FLOPS_PER_CONTACT = 8, 20
+# algorithmic HBM bytes per agent of the force kernel in the FP32 form: own
+# record (16) + sorted->storage index (4) + flags and contacts in/out (6) +
+# position read (24) and write (24)
+FORCE_BYTES_PER_AGENT = 74
+PROFILE_FILE = os.path.join(ROOT, "profiles", "force_fp32_blobs10M.md")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000, help="agents of the blob workload")
+    ap.add_argument("--sample", type=int, default=0, help="agents of the oracle's CPU sample (0 = auto)")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2301_06984_gb300 import workloads as W
+    if n == 10_000_000:
+        return W.blobs(n=n, seed=3)
+    # same density profile with fewer agents: lengths scale by (n / 1e7)^(1/3)
+    sc = (n / 1.0e7) ** (1.0 / 3.0)
+    return W.blobs(n=n, seed=3, sigma=150.0 * sc, domain=4000.0 * sc, centre_lo=600.0 * sc, centre_hi=3400.0 * sc)
+
+
+def config(args):
+    return {
+        "workload": "blobs-%d: 8 Gaussian blobs (sigma 150 um) in [0,4000]^3 um, diameters U[9,11] um, "
+                    "R = L = 11 um, dt 0.01, max displacement 3 um, Morton re-sort every 10 iterations" % args.n,
+        "n_agents": args.n,
+        "precision": "FP32 pair force and accumulation; FP64 cutoff predicate, contact decision and positions",
+        "l2_policy": "inputs larger than L2 (about 1 GB touched per iteration vs 129 MB L2); no flush",
+        "parallelism": "replica per GPU" if args.gpus > 1 else "single GPU",
+    }
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [l for l in out.splitlines() if l.strip()]
+        return False
+
+    def summary(self):
+        if not getattr(self, "lines", None):
+            return None
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        busy = [v for v in sm if mx and v > 0.5 * mx] or sm
+        return {"sm_mhz": statistics.median(busy), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- helpers
+def force_source_sha():
+    h = hashlib.sha256()
+    for f in ("force.cu", "bdm_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2301_06984_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """dram bytes per force launch from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    try:
+        text = open(PROFILE_FILE).read()
+    except OSError:
+        return None, None
+    m_sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
+    m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
+    if not m_sha or not m_b or m_sha.group(1) != force_source_sha():
+        return None, (m_sha.group(1) if m_sha else None)
+    return float(m_b.group(1)), m_sha.group(1)
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def cpu_baseline(n_sample, n_steps=1):
+    """The FP64 oracle, as it stands, on one host core over a same-density
+    sample of the blob workload."""
+    from oracle import oracle as O
+    w = workload(n_sample)
+    P = O.make_params(R=11.0, L=11.0, dt=0.01, dmax=3.0, sort_every=10, seed=3)
+    s = O.State(w.x, w.y, w.z, w.diam)
+    O.lib()
+    t0 = time.perf_counter()
+    s.step(P, n_steps)
+    dt = time.perf_counter() - t0
+    return n_sample * n_steps / dt, dt
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    n_s = args.sample or int(min(1_000_000, max(100_000, 1.5e7 / max(1, args.steps + args.warmup))))
+    from oracle import oracle as O
+    w = workload(n_s)
+    P = O.make_params(R=11.0, L=11.0, dt=0.01, dmax=3.0, sort_every=10, seed=3)
+    s = O.State(w.x, w.y, w.z, w.diam)
+    O.lib()
+    s.step(P, args.warmup)
+    t0 = time.perf_counter()
+    s.step(P, args.steps)
+    dt = time.perf_counter() - t0
+    v = n_s * args.steps / dt
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d iterations of the FP64 oracle over a %d-agent blob workload of the same "
+                                   "density (lengths scaled by (n/1e7)^(1/3)), one host core" % (args.steps, n_s)},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    from paper_2301_06984_gb300 import bdm
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    w = workload(args.n)
+    stream = torch.cuda.current_stream()
+    sim = bdm.Simulation.from_workload(w, precision="fp32", sort_every=10)
+    sim.set_workload(w)
+    sim.step(max(3, args.warmup))
+    torch.cuda.synchronize()
+
+    # ---- timed region: the production path (one CUDA graph per iteration)
+    c0 = sim.counters()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n_before = c0["n_agents"]
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        sim.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    c1 = sim.counters()
+    launches = c1["kernels_launched"] - c0["kernels_launched"]
+    updates = n_before * args.steps  # no agents are added in this workload
+    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        tm = t[:1].clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        tu = t[1:].clone()
+        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+        ms, updates = float(tm.item()), float(tu.item())
+    value = updates / (ms * 1e-3)
+
+    # ---- live per-kernel timing over a profiled pass of the same iteration
+    kp = max(1, min(args.steps, 10))
+    sim.profile_begin()
+    cand = cont = agents = 0
+    for _ in range(kp):
+        sim.step(1)
+        c = sim.counters()
+        cand += c["n_candidates"]
+        cont += c["n_contacts"]
+        agents += c["n_agents"]
+    phases = sim.profile_end()
+    force_ms = phases["force"][0] / kp
+    flops = (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont) / kp
+    clocks = clk.summary()
+    peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = flops / (force_ms * 1e-3) / 1e12
+    traffic, sha = committed_traffic()
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs")
+    roofline = {"bound": "alu", "kernel": "k_force<FP32,STEP>", "achieved": achieved, "peak": peak_alu,
+                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal, derived)",
+                "flops_per_launch": flops,
+                "hbm_view": {"achieved_gbs": FORCE_BYTES_PER_AGENT * agents / kp / (force_ms * 1e-3) / 1e9,
+                             "peak_gbs": hbm, "peak_source": "of measured" if hbm else None}}
+    phase_ms = {k: round(v[0] / kp, 4) for k, v in phases.items()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(args),
+        "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "phases_ms_per_step": phase_ms,
+        "counters_last_step": {k: c1[k] for k in ("n_agents", "n_candidates", "n_neighbors", "n_contacts",
+                                                  "n_exact_fallback", "n_occupied_bricks", "max_brick_agents")},
+    }
+
+    # ---- plain FP64 form on the same workload
+    if not args.no_fp64:
+        s64 = bdm.Simulation.from_workload(w, precision="fp64", sort_every=10)
+        s64.set_workload(w)
+        s64.step(1)
+        k64 = max(1, min(3, args.steps))
+        torch.cuda.synchronize()
+        e0.record(stream)
+        s64.step(k64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        line["fp64_form"] = {"value": args.n * k64 / (ms64 * 1e-3), "unit": UNIT, "ms_per_step": ms64 / k64,
+                             "steps": k64, "warmup": 1}
+        s64.close()
+
+    # ---- end to end through the C ABI with pinned host buffers
+    if not args.no_e2e:
+        n = args.n
+        L = bdm.lib()
+        hx = torch.empty(3 * n, dtype=torch.float64, pin_memory=True)
+        hd = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        hx.numpy()[:] = np.concatenate([w.x, w.y, w.z])
+        hd.numpy()[:] = w.diam
+        se = bdm.Simulation.from_workload(w, precision="fp32", sort_every=10)
+        ke = max(1, min(args.steps, 10))
+        nout, st, nu = C.c_int64(), C.c_int64(), C.c_uint64()
+        px, pd = C.c_void_p(hx.data_ptr()), C.c_void_p(hd.data_ptr())
+
+        def e2e_step(t):
+            se._check(L.bdm_set_agents(se._h, n, px, pd, None, None, None, None, t, n, bdm.BDM_HOST))
+            se.step(1)
+            se._check(L.bdm_get_agents(se._h, n, px, None, None, None, None, None, C.byref(nout), C.byref(st),
+                                       C.byref(nu), bdm.BDM_HOST))
+
+        for t in range(2):
+            e2e_step(t)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        for t in range(ke):
+            e2e_step(2 + t)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mse = e0.elapsed_time(e1)
+        tt = torch.tensor([mse], dtype=torch.float64, device="cuda")
+        if dist is not None:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * n * ke / (float(tt.item()) * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 24 * n, "steps": ke}
+        se.close()
+
+    # ---- FP64 oracle on the host cores (rank 0, N = 1 only)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n_s = args.sample or 1_000_000
+        v, dt = cpu_baseline(n_s)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one iteration of the FP64 oracle over a %d-agent blob workload of the "
+                                          "same density (lengths scaled by (n/1e7)^(1/3)), %.1f s on one host "
+                                          "core" % (n_s, dt)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

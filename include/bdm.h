@@ -1,0 +1,226 @@
+/*
+ * bdm.h -- C ABI of the GB300 (sm_103a) mechanical-interaction iteration for
+ * spherical agents, after BioDynaMo (Breitwieser et al., PPoPP'23,
+ * arXiv 2301.06984).
+ *
+ * One iteration (Algorithm 1 of the paper, specialised to the mechanics
+ * operation) is, in this order:
+ *   1. on sort steps, a stable reorder of the agents by the Morton code of
+ *      their uniform-grid box (Sec. 4.2, agent sorting);
+ *   2. the uniform-grid build on the current positions (Sec. 3.1): box edge
+ *      L >= R, per-axis box floor((p - lo) / L), a one-box margin so that every
+ *      3x3x3 stencil stays inside, agents of a box in ascending storage index;
+ *   3. static-agent detection (Sec. 5, conditions i-iv, made box-granular);
+ *   4. for every non-static agent, the sum over the 27 surrounding boxes of the
+ *      overlap force F = k*delta - gamma*sqrt(rbar*delta) along the centre line
+ *      (delta = r_i + r_j - d > 0, rbar = r_i r_j / (r_i + r_j); the paper
+ *      defers to the Cortex3D force without a formula, Sec. 5), for neighbours
+ *      with d^2 < R^2, j != i; displacement dt * sum F unless |sum F| <=
+ *      adherence, clamped to max_displacement; every force reads the
+ *      positions at the start of the iteration;
+ *   5. behaviours: random walk (added after the clamp), growth, and division
+ *      into two daughters;
+ *   6. the parallel merge of the daughters (Sec. 3.2, additions committed at
+ *      the end of the iteration): daughter slot = n + (number of dividing
+ *      agents with a smaller storage index), uid = next_uid + that rank.
+ *
+ * Memory: the simulation owns all device memory it uses (sized at
+ * bdm_create / bdm_set_agents from `capacity`); it never keeps a pointer the
+ * caller passed.  Pointers tagged BDM_DEVICE must be device memory valid on
+ * the simulation's stream; pointers tagged BDM_HOST are host memory (pinned
+ * memory makes the copies asynchronous).  Agent arrays are structure-of-arrays
+ * in storage order.
+ *
+ * Errors: every int-returning call returns BDM_OK (0) or a negative BDM_E*
+ * code, and bdm_last_error() gives a message.  A failed bdm_step leaves the
+ * state of the last completed iteration.  Calls on one simulation are not
+ * thread-safe; different simulations are independent.
+ */
+#ifndef BDM_H
+#define BDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BDM_OK 0
+#define BDM_EINVAL (-1)    /* bad argument (NULL, negative size, non-finite input, L < R) */
+#define BDM_ENOMEM (-2)    /* device or host allocation failed                             */
+#define BDM_ECUDA (-3)     /* a CUDA call failed (message holds the CUDA error string)     */
+#define BDM_ECAPACITY (-4) /* agents (with daughters) would exceed `capacity`              */
+#define BDM_ETIMEOUT (-5)  /* a bounded device-side wait gave up                           */
+#define BDM_ESTATE (-6)    /* call out of order (e.g. bdm_step before bdm_set_agents)       */
+
+/* precision forms */
+#define BDM_FP64 0       /* all pair arithmetic in FP64; bit-identical to the FP64 oracle */
+#define BDM_FP32_FORCE 1 /* FP32 pair arithmetic and accumulation; FP64 cutoff predicate,
+                            FP64 contact decision and FP64 positions; diameters in FP32  */
+
+/* memory tags */
+#define BDM_HOST 0
+#define BDM_DEVICE 1
+
+/* per-agent behaviour bits */
+#define BDM_BEH_GROW 1u /* volume += growth_per_step; divide at divide_volume     */
+#define BDM_BEH_WALK 2u /* random walk of walk_step um after the clamp            */
+
+typedef struct bdm_sim bdm_sim;
+
+typedef struct {
+  double interaction_radius; /* R (um); neighbour iff d^2 < R^2 (strict), j != i      */
+  double box_edge;           /* L (um) >= R; 0 selects L = R                          */
+  double dt;                 /* time step (used when dt_per_sim is NULL)              */
+  double max_displacement;   /* clamp of |dt * sum F| (um)                            */
+  double k, gamma;           /* force constants (2, 1)                                */
+  double adherence;          /* no displacement while |sum F| <= adherence (0)        */
+  int32_t precision;         /* BDM_FP64 or BDM_FP32_FORCE                            */
+  int32_t detect_static;     /* skip agents proven static (Sec. 5)                    */
+  int32_t sort_every;        /* Morton reorder when step % sort_every == 0; 0 = never */
+  int32_t n_sims;            /* >= 1: independent simulations advanced together       */
+  const double *dt_per_sim;  /* host array of n_sims time steps, or NULL              */
+  uint64_t seed;             /* Philox4x64-10 key of all in-iteration random draws     */
+  double growth_per_step;    /* um^3 added per iteration to BDM_BEH_GROW agents       */
+  double divide_volume;      /* divide when the grown volume >= this (um^3)           */
+  double ratio_lo, ratio_hi; /* daughter volume ratio uniform in [lo, hi)             */
+  double walk_step;          /* um per iteration for BDM_BEH_WALK agents              */
+  int64_t capacity;          /* maximum number of agents, daughters included          */
+  int32_t keep_forces;       /* 1: keep each iteration's summed forces (debug output) */
+  int32_t reserved;
+} bdm_params;
+
+typedef struct {
+  int64_t n_agents;           /* current number of agents                          */
+  int64_t step;               /* iterations completed                              */
+  uint64_t next_uid;          /* uid the next daughter receives                    */
+  int64_t n_static;           /* agents skipped as static in the last iteration     */
+  int64_t n_moved;            /* agents whose position changed                     */
+  int64_t n_divided;          /* divisions in the last iteration                   */
+  int64_t n_candidates;       /* pairs examined in the 27-box stencils             */
+  int64_t n_neighbors;        /* pairs with d^2 < R^2                              */
+  int64_t n_contacts;         /* neighbour pairs with delta > 0                    */
+  int64_t n_exact_fallback;   /* FP32 form: pairs decided by the FP64 path          */
+  int64_t n_boxes;            /* boxes of the grid (all simulations)               */
+  int64_t n_bricks;           /* 4x4x4-box bricks of the grid                      */
+  int64_t n_occupied_bricks;  /* bricks holding at least one agent                 */
+  int64_t max_brick_agents;   /* most agents in one brick                          */
+  int64_t kernels_launched;   /* CUDA kernels this simulation has launched so far   */
+  int32_t history_valid;      /* static detection has the previous iteration       */
+  int32_t error;              /* sticky device error word (0 = none)               */
+} bdm_counters;
+
+/* Create a simulation.  `stream` is a cudaStream_t (NULL = legacy default
+ * stream); all work of this simulation is ordered on it.  On success *out
+ * owns device memory for params->capacity agents.
+ * Errors: BDM_EINVAL (R <= 0, L < R, n_sims < 1, capacity < 1, precision
+ * unknown, growth with n_sims > 1 or with BDM_FP32_FORCE), BDM_ENOMEM,
+ * BDM_ECUDA. */
+int bdm_create(const bdm_params *params, void *stream, bdm_sim **out);
+
+/* Replace the agent population (the paper's model initialisation, Algorithm
+ * 1).  xyz: 3 x n doubles (x[0..n), y[0..n), z[0..n)); diam: n doubles (um;
+ * rounded to float in BDM_FP32_FORCE); vol: n doubles or NULL (= pi/6 d^3);
+ * uid: n or NULL (= 0..n-1); behavior: n bytes of BDM_BEH_* bits or NULL
+ * (= BDM_BEH_GROW if growth_per_step > 0, plus BDM_BEH_WALK if walk_step > 0); sim_offsets: n_sims + 1 increasing offsets starting at 0 and ending at
+ * n, or NULL when n_sims == 1; step and next_uid restore the iteration counter
+ * and the uid counter (checkpoint/resume).  The history of static detection
+ * starts empty, so no agent is static in the first iteration after this call.
+ * Errors: BDM_EINVAL (n < 0, NULL xyz/diam with n > 0, non-finite or
+ * non-positive diameter, non-finite position, bad offsets), BDM_ECAPACITY
+ * (n > capacity), BDM_ECUDA. */
+int bdm_set_agents(bdm_sim *sim, int64_t n, const double *xyz, const double *diam, const double *vol,
+                   const uint64_t *uid, const uint8_t *behavior, const int64_t *sim_offsets, int64_t step,
+                   uint64_t next_uid, int mem);
+
+/* Advance n_steps iterations (the per-iteration work is one captured CUDA
+ * graph replayed on the simulation's stream).  Blocks until the iterations
+ * are done and the device counters are read back.  Errors: BDM_ESTATE (no
+ * agents set), BDM_EINVAL (n_steps < 0), BDM_ECAPACITY (daughters would
+ * exceed capacity; the state is that of the last completed iteration),
+ * BDM_ECUDA. */
+int bdm_step(bdm_sim *sim, int n_steps);
+
+/* Reorder the agents now by the Morton code of their box in the grid of the
+ * current positions (stable: equal codes keep storage order), as a sort step
+ * does.  Errors: BDM_ESTATE, BDM_ECUDA. */
+int bdm_sort(bdm_sim *sim);
+
+/* Copy the state out (storage order).  Any output pointer may be NULL.  cap
+ * is the number of agents the arrays hold (xyz holds 3 x cap, x at 0, y at
+ * cap, z at 2 cap); sim_offsets holds n_sims + 1.  *n_out gets the number of
+ * agents.  Errors: BDM_ECAPACITY (cap < n; nothing written but *n_out),
+ * BDM_EINVAL, BDM_ECUDA. */
+int bdm_get_agents(bdm_sim *sim, int64_t cap, double *xyz, double *diam, double *vol, uint64_t *uid,
+                   uint8_t *behavior, int64_t *sim_offsets, int64_t *n_out, int64_t *step, uint64_t *next_uid,
+                   int mem);
+
+/* Counters of the last iteration (host struct).  Errors: BDM_EINVAL, BDM_ECUDA. */
+int bdm_get_counters(bdm_sim *sim, bdm_counters *out);
+
+/* Diagnostic outputs (host or device memory per `mem` is not offered: `out` is
+ * always host memory).  `what`:
+ *   BDM_DBG_FORCES       double 3 x n: summed force of the last iteration
+ *                        (needs keep_forces; 0 for static agents)
+ *   BDM_DBG_NZ           int32 n: contacts (delta > 0) of the last iteration,
+ *                        saturated at 65535
+ *   BDM_DBG_STATIC       uint8 n: 1 if the agent was skipped as static
+ *   BDM_DBG_GRID_BOX     int32 3 x n: box coordinates of each agent in the grid
+ *                        the next iteration builds
+ *   BDM_DBG_GRID_ORDER   int64 n: storage indices in grid order (Morton order
+ *                        of the boxes, ascending storage index inside a box)
+ *   BDM_DBG_GRID_GEOMETRY double 6 x n_sims: lo[3] then box counts[3]
+ *   BDM_DBG_BRICK_RANK   int64 n: Morton rank of each agent's 4x4x4 brick
+ *                        among the bricks of its simulation's grid
+ *   BDM_DBG_NEIGHBORS    int64: n + 1 CSR offsets then the neighbour storage
+ *                        indices of every agent in the canonical stencil order
+ *   BDM_DBG_FORCES_NOW   double 3 x n then int32 n (contacts) then int32 n
+ *                        (neighbours): forces on the current state without
+ *                        moving anything and without the static skip; cap and
+ *                        *n_out count 8-byte words (4 n)
+ * cap is the capacity of `out` in elements of its type; *n_out gets the number
+ * of elements needed.  Errors: BDM_ECAPACITY (cap too small; nothing written),
+ * BDM_EINVAL, BDM_ESTATE, BDM_ECUDA. */
+#define BDM_DBG_FORCES 1
+#define BDM_DBG_NZ 2
+#define BDM_DBG_STATIC 3
+#define BDM_DBG_GRID_BOX 4
+#define BDM_DBG_GRID_ORDER 5
+#define BDM_DBG_GRID_GEOMETRY 6
+#define BDM_DBG_BRICK_RANK 7
+#define BDM_DBG_NEIGHBORS 8
+#define BDM_DBG_FORCES_NOW 9
+int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out);
+
+/* Phase profiling.  After bdm_profile_begin, bdm_step launches each
+ * iteration kernel by kernel (no graph) with a CUDA event before every phase
+ * on the simulation's stream; bdm_profile_end waits for the work, writes per
+ * phase the summed device milliseconds and the kernel launches (arrays of at
+ * least `cap` entries, phase order of bdm_phase_name), sets *n_phases to the
+ * number of phases and stops profiling.  Errors: BDM_EINVAL, BDM_ECUDA. */
+int bdm_profile_begin(bdm_sim *sim);
+int bdm_profile_end(bdm_sim *sim, double *ms, int64_t *launches, int cap, int *n_phases);
+
+/* Name of phase `phase` (0-based) of an iteration: "geometry", "brick_rank",
+ * "keys", "brick_scan", "scatter", "brick_sort", "gather", "force", "divide",
+ * "finish"; "" outside the range. */
+const char *bdm_phase_name(int phase);
+
+/* Change the stream all later work of this simulation is ordered on. */
+int bdm_set_stream(bdm_sim *sim, void *stream);
+
+/* Release everything the simulation owns.  NULL-safe. */
+void bdm_destroy(bdm_sim *sim);
+
+/* Message of the last failed call on `sim` (or of the last failed
+ * bdm_create when sim is NULL).  Never NULL; valid until the next call. */
+const char *bdm_last_error(const bdm_sim *sim);
+
+/* ABI version of this header (major * 100 + minor). */
+int bdm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BDM_H */

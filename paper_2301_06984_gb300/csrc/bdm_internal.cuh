@@ -1,0 +1,265 @@
+// bdm_internal.cuh -- device data layout, shared device helpers and kernel
+// launchers of the GB300 mechanical-interaction iteration.
+//
+// Data layout in HBM (structure of arrays, storage order, capacity `cap`):
+//   X[b][axis]  double   two position buffers; buffer t % 2 holds P_t, buffer
+//                        (t + 1) % 2 holds P_(t-1) (read by the static marking)
+//   diam        double (FP64 form) or float (FP32-force form)
+//   vol, uid, beh, flags, nz   per-agent state and static-detection history
+// Grid of one iteration (Sec. 3.1), in Morton order (Sec. 4.2):
+//   boxes are grouped in 4x4x4 bricks; a brick's Morton rank among the
+//   in-domain bricks orders the bricks, the 6-bit Morton code of the box inside
+//   the brick orders the boxes; key = brick rank * 64 + local code.  Agents are
+//   counting-sorted into bricks, then each occupied brick is sorted by (box,
+//   storage index) on chip, so a box is a contiguous range of sorted positions.
+//   c32[k] (float4: box-local x, y, z, radius) and, in the FP64 form,
+//   c64[k] (dbl4: x, y, z, radius) hold the agent at sorted position k.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define BDM_MAX_SIMS_SMEM 1024
+
+// 32-byte aligned (x, y, z, w) record of doubles
+struct __align__(32) dbl4 {
+  double x, y, z, w;
+};
+__host__ __device__ __forceinline__ dbl4 mk_dbl4(double x, double y, double z, double w) {
+  dbl4 r;
+  r.x = x; r.y = y; r.z = z; r.w = w;
+  return r;
+}
+
+// device error word (sticky; kernels return early once it is set)
+enum DevError : int32_t {
+  DEV_OK = 0,
+  DEV_ECAP_BRICKS = 1,  // grid has more bricks than allocated (host regrows)
+  DEV_ECAP_OCC = 2,     // more occupied bricks than allocated (host regrows)
+  DEV_ECAP_AGENTS = 3,  // daughters would exceed the agent capacity
+  DEV_ERANGE = 4,       // a simulation spans more than 2^21 boxes per axis
+  DEV_EBOX = 5,         // more than BDM_MAX_BOX_AGENTS agents in one box
+  DEV_ENONFINITE = 6,   // a position became non-finite
+};
+
+#define BDM_MAX_BOX_AGENTS 65536
+
+// agent flag bits
+#define FL_CHANGED 1u  // moved, resized or created during the previous iteration
+#define FL_MOVED 2u    // position changed during the previous iteration
+#define FL_STATIC 4u   // skipped as static in the last iteration
+#define FL_DIVIDE 8u   // divides in the current iteration (scratch)
+
+#define BEH_GROW 1u
+#define BEH_WALK 2u
+
+struct AgentSet {
+  double *x[2], *y[2], *z[2];
+  void *diam;  // double* or float*
+  double *vol;
+  uint64_t *uid;
+  uint8_t *beh;
+  uint8_t *flags;
+  uint16_t *nz;
+};
+
+struct SimGeom {
+  double lo[3];         // grid origin per axis
+  int32_t nb[3];        // boxes per axis
+  int32_t nr[3];        // bricks per axis
+  int64_t brick_base;   // first global brick index of this simulation
+  int64_t n_bricks;     // bricks of this simulation
+  int32_t levels;       // Morton levels of the brick grid
+  int32_t pad0;
+  float lo_f[3];        // lo truncated to float (fast box path)
+  float pad1;
+  long long lo_fix[3];  // lo in fixed point (scale 2^fix_shift)
+  double dt;            // time step
+  float dt_f;
+  float pad2;
+};
+
+struct DevCounters {
+  long long n;          // agents
+  long long step;       // iterations completed
+  unsigned long long next_uid;
+  int32_t error;
+  int32_t history_valid;
+  long long total_bricks, total_boxes, n_occ, n_div, max_brick;
+  long long need_bricks, need_occ;
+  int32_t sort_now, force_sort;
+  unsigned long long work_next;  // dynamic brick fetch of the force kernel
+  // per-iteration accumulators (reset by the geometry kernel)
+  unsigned long long a_static, a_moved, a_cand, a_nbr, a_contact, a_exact;
+  // snapshot of the last completed iteration
+  unsigned long long l_static, l_moved, l_cand, l_nbr, l_contact, l_exact, l_div;
+  long long l_boxes, l_bricks, l_occ, l_max_brick;
+};
+
+struct DevParams {
+  double R, R2, L;
+  double dt, dmax, k, gamma, adherence;
+  double growth, divide_volume, ratio_lo, ratio_hi, walk_step;
+  uint64_t seed;
+  float Rf, R2_lo_f, R2_hi_f, Lf;   // FP32 prefilter: certain neighbour / certain not
+  float cband1, cband2;             // contact band: W = cband1 * s + cband2 * s^2
+  float kf, gammaf, dmaxf, adherencef, walkf, invLf;
+  float box_eps;                    // relative error bound of the fast box path
+  float graze;                      // FP32 overlaps below this (um) are "grazing"
+  float graze_e;                    // error bound of an FP32 overlap (um)
+  float rel_tol, abs_tol;           // FP32-form force tolerance the refinement keeps
+  int32_t fix_shift;                // fixed-point scale bits of the local coordinates
+  long long L_fix;                  // box edge in fixed point (multiple of 128)
+  int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk;
+  int32_t pad;
+};
+
+// Everything a kernel reaches, passed by value.
+struct DevBufs {
+  AgentSet *A;          // device-resident current agent set (swapped by the sort)
+  AgentSet *A_alt;      // device-resident other set
+  DevCounters *ctr;
+  SimGeom *geom;
+  long long *sim_off;   // n_sims + 1 (static in ensembles)
+  long long *brick_base;// n_sims + 1
+  unsigned long long *bbox;  // [2][n_sims][6] order-preserving encodings
+  int32_t *brick_table;      // (sim, linear brick) -> global brick rank
+  uint32_t *brick_count, *brick_start;
+  int32_t *brick_occ;        // global brick rank -> occupied index or -1
+  unsigned long long *dirty; // global brick rank -> 64-box dirty mask
+  int32_t *occ_list;         // occupied index -> global brick rank
+  int4 *occ_info;            // occupied index -> (Bx, By, Bz, sim)
+  uint32_t *box_start, *box_cnt;  // occupied index * 64 + local code
+  uint32_t *key, *arrival, *bucket, *perm;
+  float4 *c32;
+  dbl4 *c64;
+  uint32_t *scan_a, *scan_b;      // block partials of the scans
+  uint32_t *div_rank;
+  dbl4 *stash;                 // daughter (x, y, z, volume) by mother index
+  double *fdbg;                   // 3 x cap forces (debug)
+  int32_t *nbr_count;             // debug neighbour lists
+  long long *nbr_off;
+  long long *nbr_out;
+  int32_t *dbg_i32;               // debug: contacts / neighbours
+  long long brick_cap, occ_cap, cap, nbr_cap;
+};
+
+// ----------------------------------------------------------------- helpers
+__device__ __forceinline__ unsigned long long enc_f64(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double dec_f64(unsigned long long e) {
+  unsigned long long b = (e >> 63) ? (e & 0x7FFFFFFFFFFFFFFFull) : ~e;
+  return __longlong_as_double((long long)b);
+}
+
+// truncating double -> float through the bit pattern (error < 1 float ulp);
+// keeps the conversion off the FP64 pipe
+__device__ __forceinline__ float dtof_trunc(double v) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  unsigned hi = (unsigned)(b >> 32);
+  int e = (int)((hi >> 20) & 0x7FF);
+  int fe = e - 896;
+  if (fe <= 0 || fe >= 255) return (e == 0) ? 0.0f : __double2float_rz(v);
+  unsigned mant = (unsigned)((b >> 29) & 0x7FFFFFull);
+  return __uint_as_float((hi & 0x80000000u) | ((unsigned)fe << 23) | mant);
+}
+
+// exact float -> double through the bit pattern (normal floats and zero)
+__device__ __forceinline__ double ftod_exact(float f) {
+  unsigned u = __float_as_uint(f);
+  unsigned e = (u >> 23) & 0xFF;
+  if (e == 0 || e == 255) return (double)f;
+  unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                         ((unsigned long long)(e - 127 + 1023) << 52) |
+                         ((unsigned long long)(u & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)b);
+}
+
+// double -> fixed point (truncation of |v| * 2^s), without the FP64 pipe
+__device__ __forceinline__ long long to_fixed(double v, int s) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(v);
+  int e = (int)((b >> 52) & 0x7FF);
+  if (e == 0) return 0;
+  long long m = (long long)((b & 0xFFFFFFFFFFFFFull) | 0x10000000000000ull);
+  int sh = e - 1075 + s;
+  long long r;
+  if (sh >= 0) r = (sh > 9) ? (1ll << 62) : (m << sh);
+  else r = (sh <= -63) ? 0 : (m >> (-sh));
+  return (b >> 63) ? -r : r;
+}
+
+// 2-bit-per-axis Morton code of a box inside its brick (x low bit)
+__device__ __forceinline__ int local_code(int lx, int ly, int lz) {
+  return (lx & 1) | ((ly & 1) << 1) | ((lz & 1) << 2) | ((lx & 2) << 2) | ((ly & 2) << 3) | ((lz & 2) << 4);
+}
+__device__ __forceinline__ void local_decode(int c, int &lx, int &ly, int &lz) {
+  lx = (c & 1) | ((c >> 2) & 2);
+  ly = ((c >> 1) & 1) | ((c >> 3) & 2);
+  lz = ((c >> 2) & 1) | ((c >> 4) & 2);
+}
+
+__device__ __forceinline__ int sim_of_agent(const long long *sim_off, int n_sims, long long i) {
+  int lo = 0, hi = n_sims - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (sim_off[mid] <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Box coordinate of one axis: exactly floor(fl(fl(p - lo) / L)), the FP64
+// definition; an FP32 estimate decides whenever its error bound cannot cross
+// an integer, the FP64 path runs otherwise.
+__device__ __forceinline__ int box_axis(double p, double lo, float lo_f, const DevParams &P, bool &fallback) {
+  float pf = dtof_trunc(p);
+  float a = pf - lo_f;
+  float q = a * P.invLf;
+  float m = (fabsf(pf) + fabsf(lo_f)) * P.invLf * P.box_eps + fabsf(q) * (4.0f * 1.1920929e-7f) + 1e-30f;
+  float f0 = floorf(q - m), f1 = floorf(q + m);
+  if (f0 == f1 && fabsf(q) < 1.0e9f) {
+    fallback = false;
+    return (int)f0;
+  }
+  fallback = true;
+  double qd = floor(__ddiv_rn(__dsub_rn(p, lo), P.L));
+  if (qd < -1.0e9) return -1000000000;
+  if (qd > 1.0e9) return 1000000000;
+  return (int)qd;
+}
+
+// ----------------------------------------------------------------- launchers
+struct LaunchCfg {
+  int agent_blocks;   // grid-stride agent kernels
+  int brick_blocks;   // grid-stride brick kernels
+  int scan_blocks;    // ceil(brick_cap / SCAN_TILE)
+  int agent_scan_blocks;
+  int occ_blocks;
+  int force_blocks;
+};
+
+#define SCAN_TILE 2048
+#define SCAN_THREADS 256
+
+enum ForceMode : int32_t { FM_STEP = 0, FM_FORCES = 1, FM_COUNT_NBR = 2, FM_LIST_NBR = 3 };
+
+void launch_geometry(const DevBufs &B, const DevParams &P, cudaStream_t s);
+void launch_brick_rank(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_keys(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_brick_scan(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_scatter(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_brick_sort(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_gather(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s);
+void launch_divide(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_finish(const DevBufs &B, const DevParams &P, cudaStream_t s);
+void launch_bbox(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+void launch_debug_boxes(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int32_t *out_box,
+                        long long *out_rank, cudaStream_t s);
+void launch_diam_to_f64(const DevBufs &B, const DevParams &P, const LaunchCfg &c, double *out, cudaStream_t s);
+void launch_init_agents(const DevBufs &B, const DevParams &P, const LaunchCfg &c, const double *diam_in,
+                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n,
+                        cudaStream_t s);
+void launch_validate(const double *x, const double *y, const double *z, const double *d, long long n,
+                     int *bad, cudaStream_t s);
+void launch_nbr_offsets(const DevBufs &B, const DevParams &P, cudaStream_t s);

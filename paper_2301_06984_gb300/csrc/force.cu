@@ -1,0 +1,792 @@
+// force.cu -- the 27-box overlap force, clamped displacement, behaviours
+// (random walk, growth, division) and the parallel merge of daughters.
+//
+// Force (Sec. 5; the paper defers to the Cortex3D collision force):
+//   for neighbours j != i with d^2 < R^2 and delta = r_i + r_j - d > 0:
+//   F = k delta - gamma sqrt(rbar delta), rbar = r_i r_j / (r_i + r_j),
+//   f_i += F (p_i - p_j) / d; displacement dt * sum f unless |sum f| <=
+//   adherence, clamped to max_displacement; random walk added after the clamp.
+//
+// Work decomposition: one CTA per occupied 4x4x4 brick (fetched dynamically),
+// one warp per box.  The warp resolves the 27 stencil boxes once (lanes 0..26),
+// then takes the box's agents in groups: S lanes per agent split the candidate
+// boxes (FP32 form; S chosen per box from its occupancy and candidate count)
+// and a shuffle tree reduces the S partial sums.  The FP64 form keeps one lane
+// per agent and the canonical summation order (stencil boxes dz, dy, dx
+// ascending; ascending storage index inside a box), which makes it bit-equal
+// to the FP64 oracle.  Both forms decide "neighbour" (d^2 < R^2) and
+// "contact" (delta > 0) exactly as FP64 does: an FP32 estimate with a rigorous
+// error band decides outside the band, FP64 decides inside it.
+#include "bdm_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 64x64->128 products with the round multipliers; key bumped by the Weyl
+// constants between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+#define PURPOSE_RATIO 0ull
+#define PURPOSE_AXIS 1ull
+#define PURPOSE_WALK 2ull
+#define MAX_DRAWS 1000
+
+__device__ __forceinline__ double u53(uint64_t w) {
+  return __dmul_rn(__ull2double_rn(w >> 11), 1.0 / 9007199254740992.0);
+}
+
+// Marsaglia (1972) disc method in FP64, operation for operation as the
+// contract states it: x1, x2 = 2u - 1; accept 0 < s = x1^2 + x2^2 < 1;
+// u = (2 x1 sqrt(1-s), 2 x2 sqrt(1-s), 1 - 2 s); two attempts per block.
+__device__ void unit_vector_f64(uint64_t seed, uint64_t uid, uint64_t step, uint64_t purpose, double out[3]) {
+  for (uint64_t draw = 0; draw < MAX_DRAWS; ++draw) {
+    uint64_t c[4] = {uid, step, purpose, draw};
+    philox4x64_10(c, seed, 0ull);
+    for (int a = 0; a < 2; ++a) {
+      const double x1 = __dsub_rn(__dmul_rn(2.0, u53(c[2 * a])), 1.0);
+      const double x2 = __dsub_rn(__dmul_rn(2.0, u53(c[2 * a + 1])), 1.0);
+      const double s = __dadd_rn(__dmul_rn(x1, x1), __dmul_rn(x2, x2));
+      if (s > 0.0 && s < 1.0) {
+        const double q = __dsqrt_rn(__dsub_rn(1.0, s));
+        out[0] = __dmul_rn(__dmul_rn(2.0, x1), q);
+        out[1] = __dmul_rn(__dmul_rn(2.0, x2), q);
+        out[2] = __dsub_rn(1.0, __dmul_rn(2.0, s));
+        return;
+      }
+    }
+  }
+  out[0] = 0.0; out[1] = 0.0; out[2] = 1.0;
+}
+
+// Same accept/reject decisions as the FP64 method, taken in exact integer
+// arithmetic (x = A 2^-52 exactly; s = (A^2 + B^2) 2^-104), with FP64 only
+// when the sum lies within the FP64 rounding band around 1; the components
+// are then formed in FP32 (1 - s exact from the integers).
+__device__ void unit_vector_f32(uint64_t seed, uint64_t uid, uint64_t step, uint64_t purpose, float out[3]) {
+  for (uint64_t draw = 0; draw < MAX_DRAWS; ++draw) {
+    uint64_t c[4] = {uid, step, purpose, draw};
+    philox4x64_10(c, seed, 0ull);
+    for (int a = 0; a < 2; ++a) {
+      const long long A = (long long)(c[2 * a] >> 11) - (1ll << 52);
+      const long long Bv = (long long)(c[2 * a + 1] >> 11) - (1ll << 52);
+      const uint64_t ua = (uint64_t)(A < 0 ? -A : A), ub = (uint64_t)(Bv < 0 ? -Bv : Bv);
+      const uint64_t alo = ua * ua, ahi = __umul64hi(ua, ua);
+      const uint64_t blo = ub * ub, bhi = __umul64hi(ub, ub);
+      const uint64_t slo = alo + blo;
+      const uint64_t shi = ahi + bhi + (slo < alo ? 1ull : 0ull);
+      if (shi == 0 && slo == 0) continue;  // s == 0: reject
+      // one = 2^104 = (2^40, 0); band = 2^54 around it
+      const uint64_t one_hi = 1ull << 40;
+      // S < 2^104 - 2^54 ?
+      const bool below = (shi < one_hi - 1) || (shi == one_hi - 1 && slo < (0ull - (1ull << 54)));
+      // S > 2^104 + 2^54 ?
+      const bool above = (shi > one_hi) || (shi == one_hi && slo > (1ull << 54));
+      bool accept;
+      if (below) accept = true;
+      else if (above) accept = false;
+      else {
+        const double x1 = __dsub_rn(__dmul_rn(2.0, u53(c[2 * a])), 1.0);
+        const double x2 = __dsub_rn(__dmul_rn(2.0, u53(c[2 * a + 1])), 1.0);
+        const double s = __dadd_rn(__dmul_rn(x1, x1), __dmul_rn(x2, x2));
+        accept = (s > 0.0 && s < 1.0);
+      }
+      if (!accept) continue;
+      // 1 - s = D 2^-104 with D = 2^104 - S (exact; 0 when S >= 2^104)
+      float oms = 0.0f;
+      if (shi < one_hi) {
+        const uint64_t dlo = 0ull - slo;
+        const uint64_t dhi = one_hi - shi - (slo != 0 ? 1ull : 0ull);
+        oms = __ull2float_rn(dhi) * 9.094947e-13f /* 2^-40 */ + __ull2float_rn(dlo) * 4.9303807e-32f /* 2^-104 */;
+      }
+      const float q = sqrtf(fmaxf(oms, 0.0f));
+      const float x1f = (float)(int)(A >> 29) * 1.1920929e-7f;
+      const float x2f = (float)(int)(Bv >> 29) * 1.1920929e-7f;
+      out[0] = 2.0f * x1f * q;
+      out[1] = 2.0f * x2f * q;
+      out[2] = 2.0f * oms - 1.0f;
+      return;
+    }
+  }
+  out[0] = 0.f; out[1] = 0.f; out[2] = 1.f;
+}
+
+// Cube root by Newton's method after an exact power-of-two range reduction
+// (x = m 2^(3q), m in [0.5, 4)); six steps y <- y - (y^3 - m) / (3 y^2) from
+// the first guess 0.6 + 0.25 m, every step a single IEEE operation.
+__device__ double cbrt_newton(double x) {
+  if (x == 0.0 || !isfinite(x)) return x;
+  double sgn = 1.0;
+  if (x < 0.0) { sgn = -1.0; x = -x; }
+  int e;
+  double m = frexp(x, &e);
+  int q = e / 3, r = e % 3;
+  if (r < 0) { r += 3; q -= 1; }
+  m = ldexp(m, r);
+  double y = __dadd_rn(0.6, __dmul_rn(0.25, m));
+  for (int it = 0; it < 6; ++it) {
+    const double y2 = __dmul_rn(y, y);
+    const double y3 = __dmul_rn(y2, y);
+    y = __dsub_rn(y, __ddiv_rn(__dsub_rn(y3, m), __dmul_rn(3.0, y2)));
+  }
+  return __dmul_rn(sgn, ldexp(y, q));
+}
+
+__device__ __forceinline__ double uniform_draw(uint64_t seed, uint64_t uid, uint64_t step, uint64_t purpose) {
+  uint64_t c[4] = {uid, step, purpose, 0ull};
+  philox4x64_10(c, seed, 0ull);
+  return u53(c[0]);
+}
+
+// ---------------------------------------------------------------- pair work
+constexpr float TINY2 = 1.0e-6f;  // d^2 below this (um^2) goes to FP64
+
+template <int PREC>
+__device__ __forceinline__ dbl4 exact_of(const DevBufs &B, const AgentSet &A, int cur, unsigned k) {
+  if (PREC == 0) return B.c64[k];
+  const uint32_t i = B.perm[k];
+  return mk_dbl4(A.x[cur][i], A.y[cur][i], A.z[cur][i], ftod_exact(B.c32[k].w));
+}
+
+// FP64 pair: returns 0 not a neighbour, 1 neighbour without force, 2 contact
+// (force added to f*)
+__device__ __forceinline__ int pair_f64(const DevParams &P, const dbl4 &q, const dbl4 &c, double &fx, double &fy,
+                                        double &fz) {
+  const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+  if (!(d2 < P.R2)) return 0;
+  if (d2 == 0.0) return 1;
+  const double d = __dsqrt_rn(d2);
+  const double delta = __dsub_rn(__dadd_rn(q.w, c.w), d);
+  if (!(delta > 0.0)) return 1;
+  const double rbar = __ddiv_rn(__dmul_rn(q.w, c.w), __dadd_rn(q.w, c.w));
+  const double F = __dsub_rn(__dmul_rn(P.k, delta), __dmul_rn(P.gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
+  const double sc = __ddiv_rn(F, d);
+  fx = __dadd_rn(fx, __dmul_rn(sc, ddx));
+  fy = __dadd_rn(fy, __dmul_rn(sc, ddy));
+  fz = __dadd_rn(fz, __dmul_rn(sc, ddz));
+  return 2;
+}
+
+__device__ __forceinline__ bool is_nbr_f64(const DevParams &P, const dbl4 &q, const dbl4 &c) {
+  const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+  return d2 < P.R2;
+}
+
+__device__ __forceinline__ unsigned long long wmin64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (w < v) ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ unsigned long long wmax64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = (w > v) ? w : v;
+  }
+  return v;
+}
+__device__ __forceinline__ unsigned long long wsum64(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P, int nxt, int sim,
+                                           unsigned long long bmin[3], unsigned long long bmax[3]) {
+  unsigned long long v[6];
+  for (int d = 0; d < 3; ++d) { v[d] = wmin64(bmin[d]); v[3 + d] = wmax64(bmax[d]); }
+  if ((threadIdx.x & 31) == 0 && sim >= 0 && v[0] != ~0ull) {
+    unsigned long long *bb = B.bbox + ((size_t)nxt * P.n_sims + sim) * 6;
+    for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], v[d]); atomicMax(&bb[3 + d], v[3 + d]); }
+  }
+  for (int d = 0; d < 3; ++d) { bmin[d] = ~0ull; bmax[d] = 0ull; }
+}
+
+template <int PREC, int MODE>
+__global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
+  __shared__ int s_nocc[27];
+  __shared__ unsigned long long s_ndirty[27];
+  __shared__ int s_next;
+  __shared__ long long s_o;
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
+  const long long n_occ = C->n_occ;
+  const int lane = threadIdx.x & 31;
+  const long long step = C->step;
+  unsigned long long c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
+  int wsim = -1;
+  unsigned long long bmin[3] = {~0ull, ~0ull, ~0ull}, bmax[3] = {0ull, 0ull, 0ull};
+
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_o = (long long)atomicAdd((unsigned long long *)&C->work_next, 1ull);
+      s_next = 0;
+    }
+    __syncthreads();
+    const long long o = s_o;
+    if (o >= n_occ) break;
+    const int4 info = B.occ_info[o];
+    const SimGeom &G = B.geom[info.w];
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x;
+      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
+      int occ = -1;
+      unsigned long long dm = 0ull;
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
+        occ = B.brick_occ[rank];
+        if (use_static) dm = B.dirty[rank];
+      }
+      s_nocc[t] = occ;
+      s_ndirty[t] = dm;
+    }
+    __syncthreads();
+    if (MODE == FM_STEP && info.w != wsim) {
+      flush_bbox(B, P, nxt, wsim, bmin, bmax);
+      wsim = info.w;
+    }
+    const double dt = G.dt;
+    const float dt_f = G.dt_f;
+
+    while (true) {
+      int lb = 0;
+      if (lane == 0) lb = atomicAdd(&s_next, 1);
+      lb = __shfl_sync(0xffffffffu, lb, 0);
+      if (lb >= 64) break;
+      const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
+      if (nq == 0) continue;
+      int lx, ly, lz;
+      local_decode(lb, lx, ly, lz);
+      unsigned nb_st = 0, nb_cnt = 0;
+      bool nb_dirty = false;
+      if (lane < 27) {
+        const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
+        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+        const int lc = local_code(ax & 3, ay & 3, az & 3);
+        const int occ = s_nocc[bo];
+        if (occ >= 0) {
+          nb_st = B.box_start[(long long)occ * 64 + lc];
+          nb_cnt = B.box_cnt[(long long)occ * 64 + lc];
+        }
+        nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
+      }
+      const bool clean = !__any_sync(0xffffffffu, nb_dirty);
+      // lanes per agent
+      int S = 1;
+      if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
+        unsigned ctot = nb_cnt;
+        for (int of = 16; of > 0; of >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, of);
+        unsigned best = 0xffffffffu;
+        for (int s = 1; s <= 32; s <<= 1) {
+          const unsigned g = 32u / s;
+          const unsigned cost = ((nq + g - 1) / g) * ((ctot + s - 1) / s + 2u);
+          if (cost < best) { best = cost; S = s; }
+        }
+      }
+      const int sub = lane & (S - 1);
+      const unsigned G_ = 32u / S;
+      for (unsigned q0 = 0; q0 < nq; q0 += G_) {
+        const unsigned qi = q0 + (unsigned)(lane / S);
+        const bool valid = qi < nq;
+        const unsigned kq = qbase + (valid ? qi : 0u);
+        const uint32_t iq = B.perm[kq];
+        const float4 cq = B.c32[kq];
+        dbl4 dq = mk_dbl4(0.0, 0.0, 0.0, 0.0);
+        if (PREC == 0) dq = B.c64[kq];
+        const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
+        const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+        const bool compute = valid && !is_static;
+        float ffx = 0.f, ffy = 0.f, ffz = 0.f;
+        float gfx = 0.f, gfy = 0.f, gfz = 0.f, gbound = 0.f, fscale = 0.f;
+        double dfx = 0.0, dfy = 0.0, dfz = 0.0;
+        unsigned ncont = 0, nnb = 0;
+        long long lbase = 0;
+        if (MODE == FM_LIST_NBR && valid) lbase = B.nbr_off[iq];
+        if (__any_sync(0xffffffffu, compute)) {
+          for (int k = 0; k < 27; ++k) {
+            const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
+            if (cnt == 0) continue;
+            const float ox = (float)(k % 3 - 1) * P.Lf, oy = (float)((k / 3) % 3 - 1) * P.Lf,
+                        oz = (float)(k / 9 - 1) * P.Lf;
+            const float xq = cq.x - ox, yq = cq.y - oy, zq = cq.z - oz;
+            for (unsigned j = sub; j < cnt; j += S) {
+              if (!compute) continue;
+              const unsigned kj = st + j;
+              const float4 c = __ldg(&B.c32[kj]);
+              const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
+              const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+              c_cand++;
+              if (d2 >= P.R2_hi_f || kj == kq) continue;
+              if (PREC == 0) {
+                const dbl4 cj = B.c64[kj];
+                if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
+                  if (is_nbr_f64(P, dq, cj)) {
+                    if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
+                    nnb++;
+                  }
+                  continue;
+                }
+                const int r = pair_f64(P, dq, cj, dfx, dfy, dfz);
+                nnb += (r > 0);
+                ncont += (r == 2);
+                continue;
+              }
+              // FP32 form
+              const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+              if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
+                bool isn = true;
+                if (band && d2 > P.R2_lo_f) {
+                  c_exact++;
+                  isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
+                }
+                if (isn) {
+                  if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
+                  nnb++;
+                }
+                continue;
+              }
+              const float s = cq.w + c.w, s2 = s * s;
+              const float W = fmaf(s, P.cband1, s2 * P.cband2);
+              if (!band) {
+                nnb++;
+                if (d2 >= s2 + W) continue;  // certainly no contact
+                if (d2 > s2 - W) {           // contact decided in FP64
+                  c_exact++;
+                  double gx = 0.0, gy = 0.0, gz = 0.0;
+                  const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                  if (r == 2) {
+                    ncont++;
+                    ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
+                  }
+                  continue;
+                }
+                const float inv_d = rsqrtf(d2);
+                const float d = d2 * inv_d;
+                const float delta = s - d;
+                const float rbar = __fdividef(cq.w * c.w, s);
+                const float sq = sqrtf(rbar * delta);
+                const float kd = P.kf * delta, gs = P.gammaf * sq;
+                const float sc = (kd - gs) * inv_d;
+                if (delta < P.graze) {
+                  // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
+                  // so keep it apart with a bound of its FP32 error
+                  gfx = fmaf(sc, ex, gfx);
+                  gfy = fmaf(sc, ey, gfy);
+                  gfz = fmaf(sc, ez, gfz);
+                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
+                                                  P.gammaf * sqrtf(rbar * P.graze_e))
+                                          : P.gammaf * sqrtf(rbar * P.graze_e);
+                } else {
+                  ffx = fmaf(sc, ex, ffx);
+                  ffy = fmaf(sc, ey, ffy);
+                  ffz = fmaf(sc, ez, ffz);
+                }
+                fscale += kd + gs;
+                ncont++;
+              } else {
+                c_exact++;
+                double gx = 0.0, gy = 0.0, gz = 0.0;
+                const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                nnb += (r > 0);
+                if (r == 2) {
+                  ncont++;
+                  ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
+                }
+              }
+            }
+          }
+        }
+        // reduce the S partial sums of an agent
+        for (int of = S >> 1; of > 0; of >>= 1) {
+          ffx += __shfl_xor_sync(0xffffffffu, ffx, of);
+          ffy += __shfl_xor_sync(0xffffffffu, ffy, of);
+          ffz += __shfl_xor_sync(0xffffffffu, ffz, of);
+          ncont += __shfl_xor_sync(0xffffffffu, ncont, of);
+          nnb += __shfl_xor_sync(0xffffffffu, nnb, of);
+          if (PREC == 1) {
+            gfx += __shfl_xor_sync(0xffffffffu, gfx, of);
+            gfy += __shfl_xor_sync(0xffffffffu, gfy, of);
+            gfz += __shfl_xor_sync(0xffffffffu, gfz, of);
+            gbound += __shfl_xor_sync(0xffffffffu, gbound, of);
+            fscale += __shfl_xor_sync(0xffffffffu, fscale, of);
+          }
+        }
+        if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
+          // accept the grazing sum when its error bound is a small part of the
+          // agent's tolerance; otherwise redo those pairs in FP64
+          const bool refine = compute && gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol);
+          if (__any_sync(0xffffffffu, refine)) {
+            double hx = 0.0, hy = 0.0, hz = 0.0;
+            for (int k = 0; k < 27; ++k) {
+              const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
+              if (cnt == 0) continue;
+              const float ox = (float)(k % 3 - 1) * P.Lf, oy = (float)((k / 3) % 3 - 1) * P.Lf,
+                          oz = (float)(k / 9 - 1) * P.Lf;
+              const float xq = cq.x - ox, yq = cq.y - oy, zq = cq.z - oz;
+              for (unsigned j = sub; j < cnt; j += S) {
+                if (!refine) continue;
+                const unsigned kj = st + j;
+                const float4 c = __ldg(&B.c32[kj]);
+                const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                if (d2 >= P.R2_hi_f || kj == kq || d2 > P.R2_lo_f || d2 < TINY2) continue;
+                const float s = cq.w + c.w, s2 = s * s;
+                const float W = fmaf(s, P.cband1, s2 * P.cband2);
+                if (d2 >= s2 + W || d2 > s2 - W) continue;
+                const float delta = s - d2 * rsqrtf(d2);
+                if (!(delta < P.graze)) continue;
+                c_exact++;
+                pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
+              }
+            }
+            for (int of = S >> 1; of > 0; of >>= 1) {
+              hx += __shfl_xor_sync(0xffffffffu, hx, of);
+              hy += __shfl_xor_sync(0xffffffffu, hy, of);
+              hz += __shfl_xor_sync(0xffffffffu, hz, of);
+            }
+            if (refine) { gfx = (float)hx; gfy = (float)hy; gfz = (float)hz; }
+          }
+          ffx += gfx;
+          ffy += gfy;
+          ffz += gfz;
+        }
+        if (!valid || sub != 0) continue;
+        c_nbr += nnb;
+        c_cont += ncont;
+        if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
+        if (MODE == FM_LIST_NBR) continue;
+        double Fx, Fy, Fz;
+        if (PREC == 0) { Fx = dfx; Fy = dfy; Fz = dfz; }
+        else { Fx = ftod_exact(ffx); Fy = ftod_exact(ffy); Fz = ftod_exact(ffz); }
+        if (MODE == FM_FORCES) {
+          B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz;
+          B.dbg_i32[iq] = (int32_t)ncont;
+          B.dbg_i32[B.cap + iq] = (int32_t)nnb;
+          continue;
+        }
+        // ----------------------------------------------------- FM_STEP epilogue
+        const double px = A.x[cur][iq], py = A.y[cur][iq], pz = A.z[cur][iq];
+        double nx = px, ny = py, nzp = pz;
+        uint8_t nfl = 0;
+        bool write_pos = (fl & FL_MOVED) != 0;
+        if (is_static) {
+          nfl = FL_STATIC;
+          c_static++;
+          Fx = Fy = Fz = 0.0;
+        } else {
+          const uint8_t beh = A.beh[iq];
+          if (PREC == 1) {
+            float ux = 0.f, uy = 0.f, uz = 0.f;
+            const float fn2 = fmaf(ffx, ffx, fmaf(ffy, ffy, ffz * ffz));
+            if (fn2 > P.adherencef * P.adherencef) {
+              ux = dt_f * ffx; uy = dt_f * ffy; uz = dt_f * ffz;
+              const float dn2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+              if (dn2 > P.dmaxf * P.dmaxf) {
+                const float c = P.dmaxf * rsqrtf(dn2);
+                ux *= c; uy *= c; uz *= c;
+              }
+            }
+            if (P.walk && (beh & BEH_WALK)) {
+              float u[3];
+              unit_vector_f32(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
+              ux = fmaf(P.walkf, u[0], ux);
+              uy = fmaf(P.walkf, u[1], uy);
+              uz = fmaf(P.walkf, u[2], uz);
+            }
+            if (ux != 0.f) nx = __dadd_rn(px, ftod_exact(ux));
+            if (uy != 0.f) ny = __dadd_rn(py, ftod_exact(uy));
+            if (uz != 0.f) nzp = __dadd_rn(pz, ftod_exact(uz));
+          } else {
+            double ux = 0.0, uy = 0.0, uz = 0.0;
+            const double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dfx, dfx), __dmul_rn(dfy, dfy)), __dmul_rn(dfz, dfz)));
+            if (fn > P.adherence) {
+              ux = __dmul_rn(dt, dfx); uy = __dmul_rn(dt, dfy); uz = __dmul_rn(dt, dfz);
+              const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+              if (dn > P.dmax) {
+                const double c = __ddiv_rn(P.dmax, dn);
+                ux = __dmul_rn(ux, c); uy = __dmul_rn(uy, c); uz = __dmul_rn(uz, c);
+              }
+            }
+            if (P.walk && (beh & BEH_WALK)) {
+              double u[3];
+              unit_vector_f64(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
+              ux = __dadd_rn(ux, __dmul_rn(P.walk_step, u[0]));
+              uy = __dadd_rn(uy, __dmul_rn(P.walk_step, u[1]));
+              uz = __dadd_rn(uz, __dmul_rn(P.walk_step, u[2]));
+            }
+            nx = __dadd_rn(px, ux);
+            ny = __dadd_rn(py, uy);
+            nzp = __dadd_rn(pz, uz);
+          }
+          const bool moved = (nx != px) || (ny != py) || (nzp != pz);
+          bool changed = moved;
+          if (PREC == 0 && P.grow && (beh & BEH_GROW)) {
+            const double pi = 3.141592653589793;
+            const double v = __dadd_rn(A.vol[iq], P.growth);
+            changed = true;
+            if (v >= P.divide_volume) {
+              const uint64_t uid = A.uid[iq];
+              const double u0 = uniform_draw(P.seed, uid, (uint64_t)step, PURPOSE_RATIO);
+              const double rho = __dadd_rn(P.ratio_lo, __dmul_rn(__dsub_rn(P.ratio_hi, P.ratio_lo), u0));
+              const double v1 = __ddiv_rn(__dmul_rn(v, rho), __dadd_rn(1.0, rho));
+              const double v2 = __ddiv_rn(v, __dadd_rn(1.0, rho));
+              double ax[3];
+              unit_vector_f64(P.seed, uid, (uint64_t)step, PURPOSE_AXIS, ax);
+              const double rad = __dmul_rn(cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi)), 0.5);
+              const double a1 = __dmul_rn(rad, __ddiv_rn(v2, v)), a2 = __dmul_rn(rad, __ddiv_rn(v1, v));
+              const double cx = nx, cy = ny, cz = nzp;
+              nx = __dadd_rn(cx, __dmul_rn(a1, ax[0]));
+              ny = __dadd_rn(cy, __dmul_rn(a1, ax[1]));
+              nzp = __dadd_rn(cz, __dmul_rn(a1, ax[2]));
+              B.stash[iq] = mk_dbl4(__dsub_rn(cx, __dmul_rn(a2, ax[0])), __dsub_rn(cy, __dmul_rn(a2, ax[1])),
+                                         __dsub_rn(cz, __dmul_rn(a2, ax[2])), v2);
+              A.vol[iq] = v1;
+              ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v1), pi));
+              nfl |= FL_DIVIDE | FL_MOVED;
+              write_pos = true;
+            } else {
+              A.vol[iq] = v;
+              ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi));
+            }
+          }
+          if (moved) { nfl |= FL_MOVED; c_moved++; write_pos = true; }
+          if (changed) nfl |= FL_CHANGED;
+          A.nz[iq] = (uint16_t)min(ncont, 65535u);
+        }
+        if (write_pos) {
+          A.x[nxt][iq] = nx;
+          A.y[nxt][iq] = ny;
+          A.z[nxt][iq] = nzp;
+        }
+        A.flags[iq] = nfl;
+        if (P.keep_forces) { B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz; }
+        const unsigned long long e0 = enc_f64(nx), e1 = enc_f64(ny), e2 = enc_f64(nzp);
+        bmin[0] = min(bmin[0], e0); bmax[0] = max(bmax[0], e0);
+        bmin[1] = min(bmin[1], e1); bmax[1] = max(bmax[1], e1);
+        bmin[2] = min(bmin[2], e2); bmax[2] = max(bmax[2], e2);
+      }
+    }
+  }
+  if (MODE == FM_STEP) flush_bbox(B, P, nxt, wsim, bmin, bmax);
+  c_static = wsum64(c_static);
+  c_moved = wsum64(c_moved);
+  c_cand = wsum64(c_cand);
+  c_nbr = wsum64(c_nbr);
+  c_cont = wsum64(c_cont);
+  c_exact = wsum64(c_exact);
+  if (lane == 0) {
+    if (c_static) atomicAdd(&C->a_static, c_static);
+    if (c_moved) atomicAdd(&C->a_moved, c_moved);
+    if (c_cand) atomicAdd(&C->a_cand, c_cand);
+    if (c_nbr) atomicAdd(&C->a_nbr, c_nbr);
+    if (c_cont) atomicAdd(&C->a_contact, c_cont);
+    if (c_exact) atomicAdd(&C->a_exact, c_exact);
+  }
+}
+
+__global__ void k_reset_work(DevBufs B) { B.ctr->work_next = 0; }
+
+// ---------------------------------------------------------------- division merge
+// Daughter slot = n + (number of dividing agents with a smaller storage
+// index): a tile-wise exclusive scan of the divide flags in storage order.
+__device__ unsigned blk_scan(unsigned v, unsigned *sm, unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned x = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) sm[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = (lane < nw) ? sm[lane] : 0u;
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    sm[lane] = w;
+  }
+  __syncthreads();
+  const unsigned base = warp ? sm[warp - 1] : 0u;
+  *total = sm[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__global__ void k_div_reduce(DevBufs B) {
+  __shared__ unsigned sm[32];
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+  if (t0 >= n) return;
+  const AgentSet A = *B.A;
+  unsigned c = 0;
+  for (int e = 0; e < SCAN_TILE / SCAN_THREADS; ++e) {
+    const long long i = t0 + threadIdx.x * (SCAN_TILE / SCAN_THREADS) + e;
+    if (i < n) c += (A.flags[i] & FL_DIVIDE) ? 1u : 0u;
+  }
+  unsigned tot;
+  blk_scan(c, sm, &tot);
+  if (threadIdx.x == 0) B.scan_a[blockIdx.x] = tot;
+}
+
+__global__ void k_div_top(DevBufs B) {
+  __shared__ unsigned sm[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  const long long nblk = (n + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned carry = 0;
+  for (long long b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const long long b = b0 + threadIdx.x;
+    const unsigned v = (b < nblk) ? B.scan_a[b] : 0u;
+    unsigned t;
+    const unsigned e = blk_scan(v, sm, &t);
+    if (b < nblk) B.scan_a[b] = carry + e;
+    carry += t;
+  }
+  if (threadIdx.x == 0) C->n_div = carry;
+}
+
+__global__ void k_div_write(DevBufs B, DevParams P) {
+  __shared__ unsigned sm[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+  if (t0 >= n) return;
+  const AgentSet A = *B.A;
+  const int nxt = (int)((C->step & 1) ^ 1);
+  constexpr int E = SCAN_TILE / SCAN_THREADS;
+  unsigned c = 0;
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i < n) c += (A.flags[i] & FL_DIVIDE) ? 1u : 0u;
+  }
+  unsigned tot;
+  unsigned r = blk_scan(c, sm, &tot) + B.scan_a[blockIdx.x];
+  const double pi = 3.141592653589793;
+  unsigned long long bmin[3] = {~0ull, ~0ull, ~0ull}, bmax[3] = {0ull, 0ull, 0ull};
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i >= n || !(A.flags[i] & FL_DIVIDE)) continue;
+    const long long d = n + r;
+    if (d >= B.cap) {  // cannot happen when the up-front count is right; never write out of bounds
+      atomicCAS(&C->error, 0, (int)DEV_ECAP_AGENTS);
+      break;
+    }
+    const dbl4 sd = B.stash[i];
+    for (int b = 0; b < 2; ++b) { A.x[b][d] = sd.x; A.y[b][d] = sd.y; A.z[b][d] = sd.z; }
+    A.vol[d] = sd.w;
+    ((double *)A.diam)[d] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, sd.w), pi));
+    A.uid[d] = C->next_uid + r;
+    A.beh[d] = A.beh[i];
+    A.flags[d] = FL_CHANGED;
+    A.nz[d] = 0;
+    if (P.keep_forces) { B.fdbg[d] = 0.0; B.fdbg[B.cap + d] = 0.0; B.fdbg[2 * B.cap + d] = 0.0; }
+    A.flags[i] &= (uint8_t)~FL_DIVIDE;
+    const unsigned long long e0 = enc_f64(sd.x), e1 = enc_f64(sd.y), e2 = enc_f64(sd.z);
+    bmin[0] = min(bmin[0], e0); bmax[0] = max(bmax[0], e0);
+    bmin[1] = min(bmin[1], e1); bmax[1] = max(bmax[1], e1);
+    bmin[2] = min(bmin[2], e2); bmax[2] = max(bmax[2], e2);
+    ++r;
+  }
+  flush_bbox(B, P, nxt, 0, bmin, bmax);
+}
+
+__global__ void k_finish(DevBufs B) {
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long nd = C->n_div;
+  C->n += nd;
+  C->next_uid += (unsigned long long)nd;
+  C->l_static = C->a_static;
+  C->l_moved = C->a_moved;
+  C->l_cand = C->a_cand;
+  C->l_nbr = C->a_nbr;
+  C->l_contact = C->a_contact;
+  C->l_exact = C->a_exact;
+  C->l_div = (unsigned long long)nd;
+  C->l_boxes = C->total_boxes;
+  C->l_bricks = C->total_bricks;
+  C->l_occ = C->n_occ;
+  C->l_max_brick = C->max_brick;
+  C->step += 1;
+  C->history_valid = 1;
+}
+
+// neighbour-list offsets (debug): exclusive scan of per-agent counts, serial
+// per block tile, sufficient for diagnostic sizes
+__global__ void k_nbr_offsets(DevBufs B) {
+  __shared__ unsigned sm[32];
+  const long long n = B.ctr->n;
+  long long carry = 0;
+  for (long long b0 = 0; b0 < n; b0 += blockDim.x) {
+    const long long i = b0 + threadIdx.x;
+    const unsigned v = (i < n) ? (unsigned)B.nbr_count[i] : 0u;
+    unsigned t;
+    const unsigned e = blk_scan(v, sm, &t);
+    if (i < n) B.nbr_off[i] = carry + e;
+    carry += t;
+  }
+  if (threadIdx.x == 0) B.nbr_off[n] = carry;
+}
+
+}  // namespace
+
+void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
+  k_reset_work<<<1, 1, 0, s>>>(B);
+  const int g = c.force_blocks;
+#define LF(PR, MO) k_force<PR, MO><<<g, 128, 0, s>>>(B, P)
+  if (P.precision == 0) {
+    switch (mode) {
+      case FM_STEP: LF(0, FM_STEP); break;
+      case FM_FORCES: LF(0, FM_FORCES); break;
+      case FM_COUNT_NBR: LF(0, FM_COUNT_NBR); break;
+      default: LF(0, FM_LIST_NBR); break;
+    }
+  } else {
+    switch (mode) {
+      case FM_STEP: LF(1, FM_STEP); break;
+      case FM_FORCES: LF(1, FM_FORCES); break;
+      case FM_COUNT_NBR: LF(1, FM_COUNT_NBR); break;
+      default: LF(1, FM_LIST_NBR); break;
+    }
+  }
+#undef LF
+}
+
+void launch_divide(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_div_reduce<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B);
+  k_div_top<<<1, 1024, 0, s>>>(B);
+  k_div_write<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B, P);
+}
+
+void launch_finish(const DevBufs &B, const DevParams &P, cudaStream_t s) {
+  (void)P;
+  k_finish<<<1, 1, 0, s>>>(B);
+}
+
+void launch_nbr_offsets(const DevBufs &B, const DevParams &P, cudaStream_t s) {
+  (void)P;
+  k_nbr_offsets<<<1, 1024, 0, s>>>(B);
+}

@@ -1,0 +1,674 @@
+// grid.cu -- uniform-grid build of one iteration (Sec. 3.1 of the paper) as a
+// counting sort of Morton keys (Sec. 4.2), plus the sort-step gather.
+//
+//   k_geometry    per simulation: lo = floor(min/L) L - L, n = floor((max-lo)/L)+2
+//                 boxes per axis (one-box margin), 4x4x4 bricks, brick bases
+//   k_brick_rank  Morton rank of every in-domain brick (the paper's gap/offset
+//                 mapping rank = code - offset(code), evaluated per brick as a
+//                 prefix count of in-domain cells, O(levels) per brick)
+//   k_keys        box of every agent, key = brick rank * 64 + local Morton
+//                 code, warp-aggregated atomics for per-brick arrival slots,
+//                 dirty-box marking for the static contract (Sec. 5)
+//   k_scan_*      exclusive scan of per-brick counts and occupancy
+//   k_scatter     agents into their brick's bucket (arrival order)
+//   k_brick_sort  per occupied brick, on chip: order by (box, storage index),
+//                 box ranges, and the compact per-agent records the force
+//                 kernel streams (box-local FP32 coordinates and radius)
+//   k_gather      sort step: storage <- grid order for every agent array
+#include "bdm_internal.cuh"
+
+#include <cooperative_groups.h>
+
+namespace {
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// block-wide exclusive scan of one 32-bit value per thread; returns the
+// exclusive prefix, writes the block total to *total.  blockDim.x <= 1024.
+__device__ unsigned block_excl_scan(unsigned v, unsigned *smem32, unsigned *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  unsigned x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem32[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned w = (lane < nw) ? smem32[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    smem32[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  unsigned base = (warp > 0) ? smem32[warp - 1] : 0u;
+  *total = smem32[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+__device__ long long block_excl_scan64(long long v, long long *smem64, long long *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  long long x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) smem64[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    long long w = (lane < nw) ? smem64[lane] : 0ll;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      long long y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    smem64[lane] = w;
+  }
+  __syncthreads();
+  long long base = (warp > 0) ? smem64[warp - 1] : 0ll;
+  *total = smem64[nw - 1];
+  __syncthreads();
+  return base + x - v;
+}
+
+// Number of in-domain cells (x < n0, y < n1, z < n2) whose Morton code is
+// smaller than that of (x, y, z): walk the code from its top bit; every 1 bit
+// adds the in-domain cells of the lower half of the current node.
+__device__ long long morton_rank3(int x, int y, int z, int n0, int n1, int n2, int levels) {
+  long long rank = 0;
+  int lo[3] = {0, 0, 0}, sz[3], n[3] = {n0, n1, n2}, v[3] = {x, y, z};
+  sz[0] = sz[1] = sz[2] = 1 << levels;
+  for (int k = levels - 1; k >= 0; --k) {
+    const int half = 1 << k;
+    for (int a = 2; a >= 0; --a) {
+      if ((v[a] >> k) & 1) {
+        long long c = 1;
+        for (int b = 0; b < 3; ++b) {
+          int l = lo[b];
+          int h = (b == a) ? lo[b] + half : lo[b] + sz[b];
+          if (h > n[b]) h = n[b];
+          int w = h - l;
+          if (w <= 0) { c = 0; break; }
+          c *= w;
+        }
+        rank += c;
+        lo[a] += half;
+      }
+      sz[a] = half;
+    }
+  }
+  return rank;
+}
+
+__device__ __forceinline__ int sim_of_brick(const long long *base, int n_sims, long long g) {
+  int lo = 0, hi = n_sims - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (base[mid] <= g) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// --------------------------------------------------------------- geometry
+__global__ void k_geometry(DevBufs B, DevParams P) {
+  __shared__ long long s64[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const int S = P.n_sims;
+  const int par = (int)(C->step & 1);
+  const long long n = C->n;
+  long long carry = 0, boxes = 0;
+  int bad = 0;
+  for (int s0 = 0; s0 < S; s0 += blockDim.x) {
+    const int s = s0 + threadIdx.x;
+    long long nbk = 0;
+    if (s < S) {
+      const long long a0 = (S == 1) ? 0 : B.sim_off[s];
+      const long long a1 = (S == 1) ? n : B.sim_off[s + 1];
+      SimGeom *g = &B.geom[s];
+      if (a1 > a0) {
+        const unsigned long long *bb = B.bbox + ((size_t)par * S + s) * 6;
+        int nb[3], nr[3];
+        for (int d = 0; d < 3; ++d) {
+          double mn = dec_f64(bb[d]), mx = dec_f64(bb[3 + d]);
+          double lo = __dsub_rn(__dmul_rn(floor(__ddiv_rn(mn, P.L)), P.L), P.L);
+          double cnt = floor(__ddiv_rn(__dsub_rn(mx, lo), P.L)) + 2.0;
+          if (!(cnt >= 3.0 && cnt <= 2097152.0)) { bad = 1; cnt = 3.0; }
+          nb[d] = (int)cnt;
+          nr[d] = (nb[d] + 3) >> 2;
+          g->lo[d] = lo;
+          g->lo_f[d] = dtof_trunc(lo);
+          g->lo_fix[d] = to_fixed(lo, P.fix_shift);
+          g->nb[d] = nb[d];
+          g->nr[d] = nr[d];
+        }
+        int mxr = max(nr[0], max(nr[1], nr[2])), lv = 0;
+        while ((1 << lv) < mxr) ++lv;
+        g->levels = lv;
+        nbk = (long long)nr[0] * nr[1] * nr[2];
+        boxes += (long long)nb[0] * nb[1] * nb[2];
+      } else {
+        for (int d = 0; d < 3; ++d) {
+          g->lo[d] = 0.0; g->lo_f[d] = 0.f; g->lo_fix[d] = 0; g->nb[d] = 0; g->nr[d] = 0;
+        }
+        g->levels = 0;
+      }
+      g->n_bricks = nbk;
+    }
+    long long tot;
+    long long ex = block_excl_scan64(nbk, s64, &tot);
+    if (s < S) {
+      B.geom[s].brick_base = carry + ex;
+      B.brick_base[s] = carry + ex;
+    }
+    carry += tot;
+  }
+  // totals
+  __shared__ int s_bad;
+  __shared__ unsigned long long s_boxes;
+  if (threadIdx.x == 0) { s_bad = 0; s_boxes = 0; }
+  __syncthreads();
+  if (bad) atomicOr(&s_bad, 1);
+  atomicAdd(&s_boxes, (unsigned long long)boxes);
+  __syncthreads();
+  // reset the accumulator of the next positions' bounding box
+  const int np = par ^ 1;
+  for (int i = threadIdx.x; i < S * 6; i += blockDim.x) {
+    B.bbox[(size_t)np * S * 6 + i] = ((i % 6) < 3) ? ~0ull : 0ull;
+  }
+  if (threadIdx.x == 0) {
+    B.brick_base[S] = carry;
+    C->total_bricks = carry;
+    C->total_boxes = (long long)s_boxes;
+    if (s_bad) {
+      C->error = DEV_ERANGE;
+    } else if (carry > B.brick_cap) {
+      C->error = DEV_ECAP_BRICKS;
+      C->need_bricks = carry;
+    }
+    C->a_static = C->a_moved = C->a_cand = C->a_nbr = C->a_contact = C->a_exact = 0;
+    C->n_div = 0;
+    C->max_brick = 0;
+    C->n_occ = 0;
+    C->sort_now = ((P.sort_every > 0 && (C->step % P.sort_every) == 0) || C->force_sort) ? 1 : 0;
+    C->force_sort = 0;
+  }
+}
+
+__global__ void k_brick_rank(DevBufs B, DevParams P) {
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long total = C->total_bricks;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < total;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int s = (P.n_sims == 1) ? 0 : sim_of_brick(B.brick_base, P.n_sims, g);
+    const SimGeom &G = B.geom[s];
+    const long long base = G.brick_base;
+    const long long local = g - base;
+    const int ix = (int)(local % G.nr[0]);
+    const long long t = local / G.nr[0];
+    const int iy = (int)(t % G.nr[1]);
+    const int iz = (int)(t / G.nr[1]);
+    B.brick_table[g] = (int32_t)(base + morton_rank3(ix, iy, iz, G.nr[0], G.nr[1], G.nr[2], G.levels));
+    B.brick_count[g] = 0;
+    B.dirty[g] = 0ull;
+  }
+}
+
+// brick rank and local code of a (clamped or raw) box
+__device__ __forceinline__ void box_key(const DevBufs &B, const SimGeom &G, int bx, int by, int bz, int &rank,
+                                        int &lc) {
+  const int Bx = bx >> 2, By = by >> 2, Bz = bz >> 2;
+  const long long lin = ((long long)Bz * G.nr[1] + By) * G.nr[0] + Bx;
+  rank = B.brick_table[G.brick_base + lin];
+  lc = local_code(bx & 3, by & 3, bz & 3);
+}
+
+__global__ void k_keys(DevBufs B, DevParams P) {
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const long long n = C->n;
+  const int cur = (int)(C->step & 1);
+  const bool use_static = P.detect_static && C->history_valid;
+  const int lane = threadIdx.x & 31;
+  unsigned long long ndiv = 0;
+  for (long long base = blockIdx.x * (long long)blockDim.x; base < n; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const bool active = i < n;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, i);
+    const SimGeom &G = B.geom[s];
+    const double x = A.x[cur][i], y = A.y[cur][i], z = A.z[cur][i];
+    bool fb;
+    int bx = box_axis(x, G.lo[0], G.lo_f[0], P, fb);
+    int by = box_axis(y, G.lo[1], G.lo_f[1], P, fb);
+    int bz = box_axis(z, G.lo[2], G.lo_f[2], P, fb);
+    bx = min(max(bx, 1), G.nb[0] - 2);
+    by = min(max(by, 1), G.nb[1] - 2);
+    bz = min(max(bz, 1), G.nb[2] - 2);
+    int rank, lc;
+    box_key(B, G, bx, by, bz, rank, lc);
+    B.key[i] = (uint32_t)rank * 64u + (uint32_t)lc;
+    // warp-aggregated arrival slot in the brick
+    const unsigned m = __match_any_sync(mask, rank);
+    const int leader = __ffs(m) - 1;
+    unsigned slot = 0;
+    if (lane == leader) slot = atomicAdd(&B.brick_count[rank], (unsigned)__popc(m));
+    slot = __shfl_sync(m, slot, leader);
+    B.arrival[i] = slot + (unsigned)__popc(m & lanemask_lt());
+    if (use_static && (A.flags[i] & FL_CHANGED)) {
+      atomicOr(&B.dirty[rank], 1ull << lc);
+      const int o = cur ^ 1;
+      int ox = box_axis(A.x[o][i], G.lo[0], G.lo_f[0], P, fb);
+      int oy = box_axis(A.y[o][i], G.lo[1], G.lo_f[1], P, fb);
+      int oz = box_axis(A.z[o][i], G.lo[2], G.lo_f[2], P, fb);
+      if (ox >= 0 && ox < G.nb[0] && oy >= 0 && oy < G.nb[1] && oz >= 0 && oz < G.nb[2]) {
+        int r2, l2;
+        box_key(B, G, ox, oy, oz, r2, l2);
+        atomicOr(&B.dirty[r2], 1ull << l2);
+      }
+    }
+    if (P.grow && (A.beh[i] & BEH_GROW)) {
+      if (__dadd_rn(A.vol[i], P.growth) >= P.divide_volume) ndiv++;
+    }
+  }
+  if (P.grow) {
+    for (int o = 16; o > 0; o >>= 1) ndiv += __shfl_down_sync(0xffffffffu, ndiv, o);
+    if (lane == 0 && ndiv) atomicAdd((unsigned long long *)&C->n_div, ndiv);
+  }
+}
+
+// --------------------------------------------------------------- brick scan
+__global__ void k_scan_reduce(DevBufs B) {
+  __shared__ unsigned s32[32];
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long total = C->total_bricks;
+  const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+  if (t0 >= total) return;
+  unsigned sum = 0, occ = 0, mx = 0;
+  for (int e = 0; e < SCAN_TILE / SCAN_THREADS; ++e) {
+    const long long g = t0 + threadIdx.x * (SCAN_TILE / SCAN_THREADS) + e;
+    if (g < total) {
+      unsigned c = B.brick_count[g];
+      sum += c;
+      occ += (c > 0);
+      mx = max(mx, c);
+    }
+  }
+  unsigned tot;
+  block_excl_scan(sum, s32, &tot);
+  unsigned tot_occ;
+  block_excl_scan(occ, s32, &tot_occ);
+  for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax((unsigned long long *)&B.ctr->max_brick, (unsigned long long)mx);
+  if (threadIdx.x == 0) {
+    B.scan_a[blockIdx.x] = tot;
+    B.scan_b[blockIdx.x] = tot_occ;
+  }
+}
+
+__global__ void k_scan_top(DevBufs B, DevParams P) {
+  __shared__ unsigned s32[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long total = C->total_bricks;
+  const long long nblk = (total + SCAN_TILE - 1) / SCAN_TILE;
+  unsigned carry_a = 0, carry_b = 0;
+  for (long long b0 = 0; b0 < nblk; b0 += blockDim.x) {
+    const long long b = b0 + threadIdx.x;
+    unsigned va = (b < nblk) ? B.scan_a[b] : 0u, vb = (b < nblk) ? B.scan_b[b] : 0u;
+    unsigned ta, tb;
+    unsigned ea = block_excl_scan(va, s32, &ta);
+    unsigned eb = block_excl_scan(vb, s32, &tb);
+    if (b < nblk) {
+      B.scan_a[b] = carry_a + ea;
+      B.scan_b[b] = carry_b + eb;
+    }
+    carry_a += ta;
+    carry_b += tb;
+  }
+  if (threadIdx.x == 0) {
+    C->n_occ = carry_b;
+    if ((long long)carry_b > B.occ_cap) {
+      C->error = DEV_ECAP_OCC;
+      C->need_occ = carry_b;
+    } else if (P.grow && C->n + C->n_div > B.cap) {
+      C->error = DEV_ECAP_AGENTS;
+    }
+  }
+}
+
+__global__ void k_scan_down(DevBufs B) {
+  __shared__ unsigned s32[32];
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long total = C->total_bricks;
+  const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+  if (t0 >= total) return;
+  constexpr int E = SCAN_TILE / SCAN_THREADS;
+  unsigned c[E];
+  unsigned sum = 0, occ = 0;
+  for (int e = 0; e < E; ++e) {
+    const long long g = t0 + threadIdx.x * E + e;
+    c[e] = (g < total) ? B.brick_count[g] : 0u;
+    sum += c[e];
+    occ += (c[e] > 0);
+  }
+  unsigned tt;
+  unsigned ps = block_excl_scan(sum, s32, &tt) + B.scan_a[blockIdx.x];
+  unsigned po = block_excl_scan(occ, s32, &tt) + B.scan_b[blockIdx.x];
+  for (int e = 0; e < E; ++e) {
+    const long long g = t0 + threadIdx.x * E + e;
+    if (g < total) {
+      B.brick_start[g] = ps;
+      if (c[e] > 0) {
+        B.brick_occ[g] = (int32_t)po;
+        B.occ_list[po] = (int32_t)g;
+        ++po;
+      } else {
+        B.brick_occ[g] = -1;
+      }
+      ps += c[e];
+    }
+  }
+}
+
+__global__ void k_scatter(DevBufs B) {
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t r = B.key[i] >> 6;
+    B.bucket[B.brick_start[r] + B.arrival[i]] = (uint32_t)i;
+  }
+}
+
+// --------------------------------------------------------------- brick sort
+#define BS_THREADS 256
+#define BS_SMEM_M 4096
+
+// box-local compact record of agent i in its box (bx, by, bz)
+__device__ __forceinline__ void write_compact(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
+                                              const SimGeom &G, long long i, long long k, int bx, int by, int bz,
+                                              double x, double y, double z) {
+  const long long ox = G.lo_fix[0] + (long long)bx * P.L_fix;
+  const long long oy = G.lo_fix[1] + (long long)by * P.L_fix;
+  const long long oz = G.lo_fix[2] + (long long)bz * P.L_fix;
+  const float sc = __int_as_float((127 - P.fix_shift) << 23);
+  const float xl = (float)(int)(to_fixed(x, P.fix_shift) - ox) * sc;
+  const float yl = (float)(int)(to_fixed(y, P.fix_shift) - oy) * sc;
+  const float zl = (float)(int)(to_fixed(z, P.fix_shift) - oz) * sc;
+  float r;
+  double rd;
+  if (P.precision == 0) {
+    rd = __dmul_rn(((const double *)A.diam)[i], 0.5);
+    r = dtof_trunc(rd);
+    B.c64[k] = mk_dbl4(x, y, z, rd);
+  } else {
+    r = ((const float *)A.diam)[i] * 0.5f;
+  }
+  B.c32[k] = make_float4(xl, yl, zl, r);
+}
+
+__global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams P) {
+  __shared__ uint32_t s_idx[BS_SMEM_M];
+  __shared__ uint32_t s_grp[BS_SMEM_M];
+  __shared__ uint8_t s_l[BS_SMEM_M];
+  __shared__ uint8_t s_gl[BS_SMEM_M];
+  __shared__ unsigned s_cnt[64], s_off[64], s_cur[64];
+  __shared__ int s_abort;
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1);
+  const long long n_occ = C->n_occ;
+  for (long long o = blockIdx.x; o < n_occ; o += gridDim.x) {
+    const int g = B.occ_list[o];
+    const unsigned S0 = B.brick_start[g];
+    const unsigned m = B.brick_count[g];
+    const bool onchip = m <= BS_SMEM_M;
+    __syncthreads();
+    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+    if (threadIdx.x == 0) s_abort = 0;
+    __syncthreads();
+    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+      const uint32_t idx = B.bucket[S0 + k];
+      const unsigned l = B.key[idx] & 63u;
+      if (onchip) { s_idx[k] = idx; s_l[k] = (uint8_t)l; }
+      atomicAdd(&s_cnt[l], 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int lane = threadIdx.x;
+      unsigned a = s_cnt[lane], b = s_cnt[lane + 32];
+      unsigned xa = a, xb = b;
+      for (int d = 1; d < 32; d <<= 1) {
+        unsigned ya = __shfl_up_sync(0xffffffffu, xa, d), yb = __shfl_up_sync(0xffffffffu, xb, d);
+        if (lane >= d) { xa += ya; xb += yb; }
+      }
+      unsigned ta = __shfl_sync(0xffffffffu, xa, 31);
+      s_off[lane] = xa - a;
+      s_off[lane + 32] = ta + xb - b;
+      s_cur[lane] = xa - a;
+      s_cur[lane + 32] = ta + xb - b;
+      unsigned mx = max(a, b);
+      for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, d));
+      if (lane == 0 && mx > BDM_MAX_BOX_AGENTS) {
+        atomicCAS(&C->error, 0, (int)DEV_EBOX);
+        s_abort = 1;
+      }
+    }
+    __syncthreads();
+    if (s_abort) return;  // block-uniform
+    // group by box (arrival order inside a group)
+    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+      uint32_t idx;
+      unsigned l;
+      if (onchip) { idx = s_idx[k]; l = s_l[k]; }
+      else { idx = B.bucket[S0 + k]; l = B.key[idx] & 63u; }
+      const unsigned pos = atomicAdd(&s_cur[l], 1u);
+      if (onchip) { s_grp[pos] = idx; s_gl[pos] = (uint8_t)l; }
+      else B.arrival[S0 + pos] = idx;
+    }
+    __syncthreads();
+    // stable rank inside the box = members with a smaller storage index
+    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+      uint32_t idx;
+      unsigned l;
+      if (onchip) { idx = s_grp[k]; l = s_gl[k]; }
+      else { idx = B.arrival[S0 + k]; l = B.key[idx] & 63u; }
+      const unsigned lo = s_off[l], cnt = s_cnt[l];
+      unsigned r = 0;
+      if (onchip) {
+        for (unsigned q = 0; q < cnt; ++q) r += (s_grp[lo + q] < idx);
+      } else {
+        for (unsigned q = 0; q < cnt; ++q) r += (B.arrival[S0 + lo + q] < idx);
+      }
+      const long long kk = (long long)S0 + lo + r;
+      B.perm[kk] = idx;
+      const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, idx);
+      const SimGeom &G = B.geom[s];
+      const double x = A.x[cur][idx], y = A.y[cur][idx], z = A.z[cur][idx];
+      bool fb;
+      int bx = min(max(box_axis(x, G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
+      int by = min(max(box_axis(y, G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
+      int bz = min(max(box_axis(z, G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
+      write_compact(B, P, A, cur, G, idx, kk, bx, by, bz, x, y, z);
+      if (lo + r == 0) B.occ_info[o] = make_int4(bx >> 2, by >> 2, bz >> 2, s);
+    }
+    if (threadIdx.x < 64) {
+      B.box_start[o * 64 + threadIdx.x] = S0 + s_off[threadIdx.x];
+      B.box_cnt[o * 64 + threadIdx.x] = s_cnt[threadIdx.x];
+    }
+  }
+}
+
+// --------------------------------------------------------------- sort step
+__global__ void k_gather(DevBufs B, DevParams P) {
+  const DevCounters *C = B.ctr;
+  if (C->error || !C->sort_now) return;
+  const AgentSet A = *B.A, D = *B.A_alt;
+  const long long n = C->n;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const uint32_t i = B.perm[k];
+    for (int b = 0; b < 2; ++b) {
+      D.x[b][k] = A.x[b][i];
+      D.y[b][k] = A.y[b][i];
+      D.z[b][k] = A.z[b][i];
+    }
+    if (P.precision == 0) ((double *)D.diam)[k] = ((const double *)A.diam)[i];
+    else ((float *)D.diam)[k] = ((const float *)A.diam)[i];
+    if (A.vol) D.vol[k] = A.vol[i];
+    D.uid[k] = A.uid[i];
+    D.beh[k] = A.beh[i];
+    D.flags[k] = A.flags[i];
+    D.nz[k] = A.nz[i];
+    B.perm[k] = (uint32_t)k;
+  }
+}
+
+__global__ void k_swap(DevBufs B) {
+  const DevCounters *C = B.ctr;
+  if (C->error || !C->sort_now) return;
+  const AgentSet t = *B.A;
+  *B.A = *B.A_alt;
+  *B.A_alt = t;
+}
+
+// --------------------------------------------------------------- bbox / init
+__global__ void k_bbox_reset(DevBufs B, DevParams P) {
+  const int par = (int)(B.ctr->step & 1);
+  for (int i = threadIdx.x; i < P.n_sims * 6; i += blockDim.x)
+    B.bbox[(size_t)par * P.n_sims * 6 + i] = ((i % 6) < 3) ? ~0ull : 0ull;
+}
+
+__global__ void k_bbox(DevBufs B, DevParams P) {
+  const DevCounters *C = B.ctr;
+  const AgentSet A = *B.A;
+  const long long n = C->n;
+  const int par = (int)(C->step & 1);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, i);
+    unsigned long long *bb = B.bbox + ((size_t)par * P.n_sims + s) * 6;
+    const double p[3] = {A.x[par][i], A.y[par][i], A.z[par][i]};
+    for (int d = 0; d < 3; ++d) {
+      atomicMin(&bb[d], enc_f64(p[d]));
+      atomicMax(&bb[3 + d], enc_f64(p[d]));
+    }
+  }
+}
+
+__global__ void k_debug_boxes(DevBufs B, DevParams P, int32_t *out_box, long long *out_rank) {
+  const DevCounters *C = B.ctr;
+  const AgentSet A = *B.A;
+  const long long n = C->n;
+  const int cur = (int)(C->step & 1);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, i);
+    const SimGeom &G = B.geom[s];
+    bool fb;
+    int bx = min(max(box_axis(A.x[cur][i], G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
+    int by = min(max(box_axis(A.y[cur][i], G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
+    int bz = min(max(box_axis(A.z[cur][i], G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
+    out_box[i] = bx;
+    out_box[n + i] = by;
+    out_box[2 * n + i] = bz;
+    out_rank[i] = (long long)(B.key[i] >> 6) - G.brick_base;
+  }
+}
+
+__global__ void k_diam_to_f64(DevBufs B, DevParams P, double *out) {
+  const DevCounters *C = B.ctr;
+  const AgentSet A = *B.A;
+  const long long n = C->n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = (P.precision == 0) ? ((const double *)A.diam)[i] : (double)((const float *)A.diam)[i];
+}
+
+__global__ void k_init_agents(DevBufs B, DevParams P, const double *diam_in, const double *vol_in,
+                              const uint64_t *uid_in, const uint8_t *beh_in, long long n) {
+  const AgentSet A = *B.A;
+  const double pi = 3.141592653589793;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double d = diam_in[i];
+    if (P.precision == 0) ((double *)A.diam)[i] = d;
+    else ((float *)A.diam)[i] = __double2float_rn(d);
+    if (A.vol) A.vol[i] = vol_in ? vol_in[i] : __dmul_rn(__dmul_rn(__dmul_rn(pi / 6.0, d), d), d);
+    A.uid[i] = uid_in ? uid_in[i] : (uint64_t)i;
+    A.beh[i] = beh_in ? beh_in[i] : (uint8_t)((P.grow ? BEH_GROW : 0) | (P.walk ? BEH_WALK : 0));
+    A.flags[i] = 0;
+    A.nz[i] = 0;
+  }
+}
+
+__global__ void k_validate(const double *x, const double *y, const double *z, const double *d, long long n,
+                           int *bad) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = x[i], b = y[i], c = z[i], e = d[i];
+    const bool ok = isfinite(a) && isfinite(b) && isfinite(c) && fabs(a) < 1e9 && fabs(b) < 1e9 && fabs(c) < 1e9 &&
+                    isfinite(e) && e > 0.0 && e < 1e6;
+    if (!ok) atomicOr(bad, 1);
+  }
+}
+
+}  // namespace
+
+// --------------------------------------------------------------- launchers
+void launch_geometry(const DevBufs &B, const DevParams &P, cudaStream_t s) {
+  k_geometry<<<1, 1024, 0, s>>>(B, P);
+}
+void launch_brick_rank(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_brick_rank<<<c.brick_blocks, 256, 0, s>>>(B, P);
+}
+void launch_keys(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_keys<<<c.agent_blocks, 256, 0, s>>>(B, P);
+}
+void launch_brick_scan(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_scan_reduce<<<c.scan_blocks, SCAN_THREADS, 0, s>>>(B);
+  k_scan_top<<<1, 1024, 0, s>>>(B, P);
+  k_scan_down<<<c.scan_blocks, SCAN_THREADS, 0, s>>>(B);
+}
+void launch_scatter(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  (void)P;
+  k_scatter<<<c.agent_blocks, 256, 0, s>>>(B);
+}
+void launch_brick_sort(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_brick_sort<<<c.occ_blocks, BS_THREADS, 0, s>>>(B, P);
+}
+void launch_gather(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_gather<<<c.agent_blocks, 256, 0, s>>>(B, P);
+  k_swap<<<1, 1, 0, s>>>(B);
+}
+void launch_bbox(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_bbox_reset<<<1, 256, 0, s>>>(B, P);
+  k_bbox<<<c.agent_blocks, 256, 0, s>>>(B, P);
+}
+void launch_debug_boxes(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int32_t *out_box,
+                        long long *out_rank, cudaStream_t s) {
+  k_debug_boxes<<<c.agent_blocks, 256, 0, s>>>(B, P, out_box, out_rank);
+}
+void launch_diam_to_f64(const DevBufs &B, const DevParams &P, const LaunchCfg &c, double *out, cudaStream_t s) {
+  k_diam_to_f64<<<c.agent_blocks, 256, 0, s>>>(B, P, out);
+}
+void launch_init_agents(const DevBufs &B, const DevParams &P, const LaunchCfg &c, const double *diam_in,
+                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n,
+                        cudaStream_t s) {
+  k_init_agents<<<c.agent_blocks, 256, 0, s>>>(B, P, diam_in, vol_in, uid_in, beh_in, n);
+}
+void launch_validate(const double *x, const double *y, const double *z, const double *d, long long n, int *bad,
+                     cudaStream_t s) {
+  k_validate<<<1216, 256, 0, s>>>(x, y, z, d, n, bad);
+}
