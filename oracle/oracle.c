@@ -403,8 +403,9 @@ static void grid_range(const grid_t *G, int64_t key, int64_t *first, int64_t *la
 /* ------------------------------------------------------------------------ */
 typedef struct {
   double fx, fy, fz;
-  int32_t nz;  /* contacts: neighbours with delta > 0 */
-  int32_t nnb; /* neighbours: d^2 < R^2, j != i */
+  double scale; /* sum over contacts of k*delta + gamma*sqrt(rbar*delta) (tolerance base) */
+  int32_t nz;   /* contacts: neighbours with delta > 0 */
+  int32_t nnb;  /* neighbours: d^2 < R^2, j != i */
   int32_t ncoincident;
 } force_acc;
 
@@ -417,6 +418,7 @@ static void force_on(const orc_state *st, const orc_params *P, const grid_t *G, 
   double R2 = P->R * P->R;
   double xi = st->x[i], yi = st->y[i], zi = st->z[i], ri = st->diam[i] * 0.5;
   a->fx = a->fy = a->fz = 0.0;
+  a->scale = 0.0;
   a->nz = a->nnb = a->ncoincident = 0;
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
@@ -438,8 +440,10 @@ static void force_on(const orc_state *st, const orc_params *P, const grid_t *G, 
           double delta = (ri + rj) - d;
           if (!(delta > 0.0)) continue;
           double rbar = (ri * rj) / (ri + rj);
-          double F = P->k * delta - P->gamma * sqrt(rbar * delta);
+          double kd = P->k * delta, gs = P->gamma * sqrt(rbar * delta);
+          double F = kd - gs;
           double sc = F / d;
+          a->scale += kd + gs;
           a->fx = a->fx + sc * ddx;
           a->fy = a->fy + sc * ddy;
           a->fz = a->fz + sc * ddz;
@@ -570,9 +574,11 @@ int64_t orc_neighbors_brute(const orc_state *st, const orc_params *P, int64_t *o
 }
 
 /* Summed pair force on selected agents (all when q == NULL), without the
- * static skip; f is 3 x nq SoA, nz/nnb optional. */
+ * static skip; f is 3 x nq SoA; nz, nnb and scale (sum over contacts of the
+ * magnitudes of the two force terms, the base of the FP32 tolerance) are
+ * optional. */
 int orc_forces(const orc_state *st, const orc_params *P, int64_t nq, const int64_t *q, double *f,
-               int32_t *nz, int32_t *nnb) {
+               int32_t *nz, int32_t *nnb, double *scale) {
   int rc = check_state(st, P);
   if (rc) return rc;
   grid_t G;
@@ -587,6 +593,7 @@ int orc_forces(const orc_state *st, const orc_params *P, int64_t nq, const int64
     f[m] = a.fx; f[nq + m] = a.fy; f[2 * nq + m] = a.fz;
     if (nz) nz[m] = a.nz;
     if (nnb) nnb[m] = a.nnb;
+    if (scale) scale[m] = a.scale;
   }
   grid_free(&G);
   return ORC_OK;

@@ -88,7 +88,7 @@ def _declare(L):
     L.orc_neighbors.restype = C.c_int64
     L.orc_neighbors_brute.argtypes = [SP, PP, vp, vp, C.c_int64]
     L.orc_neighbors_brute.restype = C.c_int64
-    L.orc_forces.argtypes = [SP, PP, C.c_int64, vp, vp, vp, vp]
+    L.orc_forces.argtypes = [SP, PP, C.c_int64, vp, vp, vp, vp, vp]
     L.orc_forces.restype = C.c_int
     L.orc_philox4x64_10.argtypes = [vp, vp, vp]
     L.orc_philox4x64_10.restype = None
@@ -246,15 +246,19 @@ class State:
     def neighbors_brute(self, params: Params):
         return self._csr(lib().orc_neighbors_brute, params)
 
-    def forces_of(self, params: Params, q=None):
+    def forces_of(self, params: Params, q=None, with_scale=False):
         nq = self.n if q is None else len(q)
         qa = None if q is None else np.ascontiguousarray(q, dtype=np.int64)
         f = np.zeros((3, max(nq, 1)))
         nz = np.zeros(max(nq, 1), np.int32)
         nnb = np.zeros(max(nq, 1), np.int32)
-        rc = lib().orc_forces(C.byref(self._s), C.byref(params), nq, _ptr(qa), _ptr(f), _ptr(nz), _ptr(nnb))
+        sc = np.zeros(max(nq, 1))
+        rc = lib().orc_forces(C.byref(self._s), C.byref(params), nq, _ptr(qa), _ptr(f), _ptr(nz), _ptr(nnb),
+                              _ptr(sc))
         if rc != 0:
             raise RuntimeError("orc_forces failed: %d" % rc)
+        if with_scale:
+            return f[:, :nq], nz[:nq], nnb[:nq], sc[:nq]
         return f[:, :nq], nz[:nq], nnb[:nq]
 
 

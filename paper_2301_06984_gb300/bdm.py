@@ -86,7 +86,9 @@ def lib():
     """Load (building first if needed) the CUDA library; raises if impossible."""
     global _LIB
     if _LIB is None:
-        path = _build.build()
+        # BDM_LIBRARY selects an already built library (for example a build
+        # variant); otherwise the in-tree library is built if stale
+        path = os.environ.get("BDM_LIBRARY") or _build.build()
         if not os.path.exists(path):
             raise RuntimeError("CUDA library %s is missing" % path)
         L = C.CDLL(path)

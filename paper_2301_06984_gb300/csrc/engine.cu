@@ -174,7 +174,7 @@ static void make_launch_cfg(bdm_sim *s) {
   s->lc.scan_blocks = clampb((s->B.brick_cap + SCAN_TILE - 1) / SCAN_TILE, 1, 1LL << 30);
   s->lc.agent_scan_blocks = clampb((s->cap + SCAN_TILE - 1) / SCAN_TILE, 1, 1LL << 30);
   s->lc.occ_blocks = clampb(s->B.occ_cap, 1, sm * 4);
-  s->lc.force_blocks = clampb(s->B.occ_cap, 1, sm * 8);
+  s->lc.force_blocks = clampb(s->B.occ_cap, 1, sm * 4);
 }
 
 static int alloc_grid(bdm_sim *s, long long brick_cap, long long occ_cap) {

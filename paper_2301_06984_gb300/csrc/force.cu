@@ -215,23 +215,35 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
   for (int d = 0; d < 3; ++d) { bmin[d] = ~0ull; bmax[d] = 0ull; }
 }
 
+#define FORCE_WARPS 8
+#define QCAP 32
+
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
+__global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevParams P) {
   __shared__ int s_nocc[27];
   __shared__ unsigned long long s_ndirty[27];
   __shared__ int s_next;
   __shared__ long long s_o;
+  __shared__ float4 s_off[27];
+  // per-lane queues of candidates that passed the FP32 prefilter:
+  // [warp][slot][lane], so every lane writes its own bank
+  __shared__ uint32_t s_q[FORCE_WARPS][QCAP][32];
+  __shared__ uint8_t s_qk[FORCE_WARPS][QCAP][32];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
   const int cur = (int)(C->step & 1), nxt = cur ^ 1;
   const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
   const long long n_occ = C->n_occ;
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long step = C->step;
   unsigned long long c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
   int wsim = -1;
   unsigned long long bmin[3] = {~0ull, ~0ull, ~0ull}, bmax[3] = {0ull, 0ull, 0ull};
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
+  }
 
   while (true) {
     __syncthreads();
@@ -289,16 +301,16 @@ __global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
         nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
       }
       const bool clean = !__any_sync(0xffffffffu, nb_dirty);
-      // lanes per agent
+      // lanes per agent: split the candidates of small boxes over several lanes
       int S = 1;
       if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
         unsigned ctot = nb_cnt;
         for (int of = 16; of > 0; of >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, of);
         unsigned best = 0xffffffffu;
-        for (int s = 1; s <= 32; s <<= 1) {
-          const unsigned g = 32u / s;
-          const unsigned cost = ((nq + g - 1) / g) * ((ctot + s - 1) / s + 2u);
-          if (cost < best) { best = cost; S = s; }
+        for (int sl = 1; sl <= 32; sl <<= 1) {
+          const unsigned g = 32u / sl;
+          const unsigned cost = ((nq + g - 1) / g) * ((ctot + sl - 1) / sl + 2u);
+          if (cost < best) { best = cost; S = sl; }
         }
       }
       const int sub = lane & (S - 1);
@@ -321,20 +333,15 @@ __global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
         long long lbase = 0;
         if (MODE == FM_LIST_NBR && valid) lbase = B.nbr_off[iq];
         if (__any_sync(0xffffffffu, compute)) {
-          for (int k = 0; k < 27; ++k) {
-            const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
-            if (cnt == 0) continue;
-            const float ox = (float)(k % 3 - 1) * P.Lf, oy = (float)((k / 3) % 3 - 1) * P.Lf,
-                        oz = (float)(k / 9 - 1) * P.Lf;
-            const float xq = cq.x - ox, yq = cq.y - oy, zq = cq.z - oz;
-            for (unsigned j = sub; j < cnt; j += S) {
-              if (!compute) continue;
-              const unsigned kj = st + j;
-              const float4 c = __ldg(&B.c32[kj]);
-              const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
-              const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-              c_cand++;
-              if (d2 >= P.R2_hi_f || kj == kq) continue;
+          unsigned qlen = 0;
+          // evaluate the queued pairs with every lane busy; the queue keeps
+          // each lane's candidate order, so the FP64 form keeps the
+          // canonical summation order
+          auto drain = [&]() {
+            const unsigned mx = __reduce_max_sync(0xffffffffu, qlen);
+            for (unsigned m = 0; m < mx; ++m) {
+              if (m >= qlen) continue;
+              const unsigned kj = s_q[warp][m][lane];
               if (PREC == 0) {
                 const dbl4 cj = B.c64[kj];
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
@@ -349,7 +356,10 @@ __global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
                 ncont += (r == 2);
                 continue;
               }
-              // FP32 form
+              const float4 of = s_off[s_qk[warp][m][lane]];
+              const float4 c = __ldg(&B.c32[kj]);
+              const float ex = (cq.x - of.x) - c.x, ey = (cq.y - of.y) - c.y, ez = (cq.z - of.z) - c.z;
+              const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
               const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
               if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
                 bool isn = true;
@@ -363,45 +373,7 @@ __global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
                 }
                 continue;
               }
-              const float s = cq.w + c.w, s2 = s * s;
-              const float W = fmaf(s, P.cband1, s2 * P.cband2);
-              if (!band) {
-                nnb++;
-                if (d2 >= s2 + W) continue;  // certainly no contact
-                if (d2 > s2 - W) {           // contact decided in FP64
-                  c_exact++;
-                  double gx = 0.0, gy = 0.0, gz = 0.0;
-                  const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
-                  if (r == 2) {
-                    ncont++;
-                    ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
-                  }
-                  continue;
-                }
-                const float inv_d = rsqrtf(d2);
-                const float d = d2 * inv_d;
-                const float delta = s - d;
-                const float rbar = __fdividef(cq.w * c.w, s);
-                const float sq = sqrtf(rbar * delta);
-                const float kd = P.kf * delta, gs = P.gammaf * sq;
-                const float sc = (kd - gs) * inv_d;
-                if (delta < P.graze) {
-                  // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
-                  // so keep it apart with a bound of its FP32 error
-                  gfx = fmaf(sc, ex, gfx);
-                  gfy = fmaf(sc, ey, gfy);
-                  gfz = fmaf(sc, ez, gfz);
-                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
-                                                  P.gammaf * sqrtf(rbar * P.graze_e))
-                                          : P.gammaf * sqrtf(rbar * P.graze_e);
-                } else {
-                  ffx = fmaf(sc, ex, ffx);
-                  ffy = fmaf(sc, ey, ffy);
-                  ffz = fmaf(sc, ez, ffz);
-                }
-                fscale += kd + gs;
-                ncont++;
-              } else {
+              if (band) {
                 c_exact++;
                 double gx = 0.0, gy = 0.0, gz = 0.0;
                 const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
@@ -410,9 +382,74 @@ __global__ void __launch_bounds__(128) k_force(DevBufs B, DevParams P) {
                   ncont++;
                   ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
                 }
+                continue;
               }
+              nnb++;
+              const float s = cq.w + c.w, s2 = s * s;
+              const float W = fmaf(s, P.cband1, s2 * P.cband2);
+              if (d2 >= s2 + W) continue;  // certainly no contact
+              if (d2 > s2 - W) {           // contact decided in FP64
+                c_exact++;
+                double gx = 0.0, gy = 0.0, gz = 0.0;
+                const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                if (r == 2) {
+                  ncont++;
+                  ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
+                }
+                continue;
+              }
+              const float inv_d = rsqrtf(d2);
+              const float d = d2 * inv_d;
+              const float delta = s - d;
+              const float rbar = __fdividef(cq.w * c.w, s);
+              const float sq = sqrtf(rbar * delta);
+              const float kd = P.kf * delta, gs = P.gammaf * sq;
+              const float sc = (kd - gs) * inv_d;
+              if (delta < P.graze) {
+                // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
+                // so keep it apart with a bound of its FP32 error
+                gfx = fmaf(sc, ex, gfx);
+                gfy = fmaf(sc, ey, gfy);
+                gfz = fmaf(sc, ez, gfz);
+                gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
+                                                P.gammaf * sqrtf(rbar * P.graze_e))
+                                        : P.gammaf * sqrtf(rbar * P.graze_e);
+              } else {
+                ffx = fmaf(sc, ex, ffx);
+                ffy = fmaf(sc, ey, ffy);
+                ffz = fmaf(sc, ez, ffz);
+              }
+              fscale += kd + gs;
+              ncont++;
+            }
+            qlen = 0;
+            __syncwarp();
+          };
+          for (int k = 0; k < 27; ++k) {
+            const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
+            if (cnt == 0) continue;
+            const float4 of = s_off[k];
+            const float xq = cq.x - of.x, yq = cq.y - of.y, zq = cq.z - of.z;
+            for (unsigned jj = 0; jj < cnt; jj += S) {
+              const unsigned j = jj + sub;
+              const unsigned kj = st + j;
+              bool hit = false;
+              if (compute && j < cnt) {
+                const float4 c = __ldg(&B.c32[kj]);
+                const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                c_cand++;
+                hit = (d2 < P.R2_hi_f) && (kj != kq);
+              }
+              if (hit) {
+                s_q[warp][qlen][lane] = kj;
+                s_qk[warp][qlen][lane] = (uint8_t)k;
+                ++qlen;
+              }
+              if (__any_sync(0xffffffffu, qlen == QCAP)) drain();
             }
           }
+          if (__any_sync(0xffffffffu, qlen > 0)) drain();
         }
         // reduce the S partial sums of an agent
         for (int of = S >> 1; of > 0; of >>= 1) {
@@ -756,7 +793,7 @@ __global__ void k_nbr_offsets(DevBufs B) {
 void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
   k_reset_work<<<1, 1, 0, s>>>(B);
   const int g = c.force_blocks;
-#define LF(PR, MO) k_force<PR, MO><<<g, 128, 0, s>>>(B, P)
+#define LF(PR, MO) k_force<PR, MO><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
   if (P.precision == 0) {
     switch (mode) {
       case FM_STEP: LF(0, FM_STEP); break;

@@ -556,17 +556,58 @@ __global__ void k_bbox_reset(DevBufs B, DevParams P) {
 }
 
 __global__ void k_bbox(DevBufs B, DevParams P) {
+  // per-thread min/max of the encoded coordinates, flushed when the
+  // simulation changes; a single simulation reduces over the warp and the
+  // block first, so each block issues six atomics
+  __shared__ unsigned long long s_v[32][6];
   const DevCounters *C = B.ctr;
   const AgentSet A = *B.A;
   const long long n = C->n;
   const int par = (int)(C->step & 1);
+  int cs = -1;
+  unsigned long long v[6] = {~0ull, ~0ull, ~0ull, 0ull, 0ull, 0ull};
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, i);
-    unsigned long long *bb = B.bbox + ((size_t)par * P.n_sims + s) * 6;
-    const double p[3] = {A.x[par][i], A.y[par][i], A.z[par][i]};
+    if (s != cs) {
+      if (cs >= 0) {
+        unsigned long long *bb = B.bbox + ((size_t)par * P.n_sims + cs) * 6;
+        for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], v[d]); atomicMax(&bb[3 + d], v[3 + d]); }
+      }
+      cs = s;
+      v[0] = v[1] = v[2] = ~0ull;
+      v[3] = v[4] = v[5] = 0ull;
+    }
+    const unsigned long long e[3] = {enc_f64(A.x[par][i]), enc_f64(A.y[par][i]), enc_f64(A.z[par][i])};
     for (int d = 0; d < 3; ++d) {
-      atomicMin(&bb[d], enc_f64(p[d]));
-      atomicMax(&bb[3 + d], enc_f64(p[d]));
+      v[d] = min(v[d], e[d]);
+      v[3 + d] = max(v[3 + d], e[d]);
+    }
+  }
+  if (P.n_sims > 1) {
+    if (cs >= 0) {
+      unsigned long long *bb = B.bbox + ((size_t)par * P.n_sims + cs) * 6;
+      for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], v[d]); atomicMax(&bb[3 + d], v[3 + d]); }
+    }
+    return;
+  }
+  for (int o = 16; o > 0; o >>= 1)
+    for (int d = 0; d < 3; ++d) {
+      v[d] = min(v[d], __shfl_xor_sync(0xffffffffu, v[d], o));
+      v[3 + d] = max(v[3 + d], __shfl_xor_sync(0xffffffffu, v[3 + d], o));
+    }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int d = 0; d < 6; ++d) s_v[warp][d] = v[d];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < nw; ++w)
+      for (int d = 0; d < 3; ++d) {
+        v[d] = min(v[d], s_v[w][d]);
+        v[3 + d] = max(v[3 + d], s_v[w][3 + d]);
+      }
+    if (v[0] != ~0ull) {
+      unsigned long long *bb = B.bbox + (size_t)par * 6;
+      for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], v[d]); atomicMax(&bb[3 + d], v[3 + d]); }
     }
   }
 }

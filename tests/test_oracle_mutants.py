@@ -12,7 +12,7 @@ from tests import test_oracle_pins as pins
 SRC = os.path.join(os.path.dirname(build_oracle.__file__), "oracle.c")
 
 MUTANTS = {
-    "sqrt_term_sign": ("F = P->k * delta - P->gamma", "F = P->k * delta + P->gamma"),
+    "sqrt_term_sign": ("double F = kd - gs;", "double F = kd + gs;"),
     "rbar_formula": ("double rbar = (ri * rj) / (ri + rj);", "double rbar = (ri + rj) / 2.0;"),
     "cutoff_not_strict": ("if (!(d2 < R2)) continue;", "if (!(d2 <= R2)) continue;"),
     "accumulate_sign": ("a->fx = a->fx + sc * ddx;", "a->fx = a->fx - sc * ddx;"),
