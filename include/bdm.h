@@ -209,6 +209,30 @@ const char *bdm_phase_name(int phase);
 /* Change the stream all later work of this simulation is ordered on. */
 int bdm_set_stream(bdm_sim *sim, void *stream);
 
+/* Summed force on every agent of one simulation without allocating any
+ * memory.  The paper has no counterpart: this entry point serves callers that
+ * cannot call cudaMalloc -- code recorded inside a CUDA stream capture that
+ * must not allocate, host applications whose own allocator owns all device
+ * memory, plug-ins forbidden to allocate.  It runs the same grid build and
+ * force kernels as BDM_DBG_FORCES_NOW in the FP64 form (no displacement, no
+ * static skip) on the caller's device buffers: xyz 3 x n doubles (x, y, z
+ * blocks), diam n doubles; outputs forces 3 x n doubles (same layout) and
+ * counts 2 x n int32 (contacts, then neighbours).  Every intermediate lives
+ * in one fixed device array of about 23 MB, which each GPU that loads this
+ * library holds until the process exits; it bounds the problem to at most
+ * 131072 agents, 262144 4x4x4-box bricks and 16384 occupied bricks
+ * (BDM_ECAPACITY beyond them, with nothing written).  All calls share that
+ * array and it keeps the last call's contents, so calls that may overlap on
+ * the GPU (other streams, other host threads, same device) race: serialise
+ * them.  The first call on a device looks up the array's device address
+ * (once per device, with that device current); make that first call before
+ * any stream capture.  Work is ordered on `stream` (a cudaStream_t, NULL =
+ * legacy default) and the call waits for it to finish.  Errors: BDM_EINVAL,
+ * BDM_ECAPACITY, BDM_ECUDA; bdm_noalloc_last_error() gives the message. */
+int bdm_forces_noalloc(int64_t n, const double *xyz, const double *diam, double interaction_radius,
+                       double box_edge, double k, double gamma, double *forces, int32_t *counts, void *stream);
+const char *bdm_noalloc_last_error(void);
+
 /* Release everything the simulation owns.  NULL-safe. */
 void bdm_destroy(bdm_sim *sim);
 

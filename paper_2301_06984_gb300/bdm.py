@@ -75,6 +75,9 @@ SIGNATURES = {
     "bdm_profile_begin": (C.c_int, [C.c_void_p]),
     "bdm_profile_end": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)]),
     "bdm_phase_name": (C.c_char_p, [C.c_int]),
+    "bdm_forces_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "bdm_noalloc_last_error": (C.c_char_p, []),
 }
 
 

@@ -166,6 +166,9 @@ static DevParams make_dev_params(const bdm_params &P) {
   return d;
 }
 
+// device parameters of a parameter block (also used by bdm_forces_noalloc)
+DevParams make_dev_params_for(const bdm_params &P) { return make_dev_params(P); }
+
 static void make_launch_cfg(bdm_sim *s) {
   const long long sm = s->sm_count;
   auto clampb = [](long long v, long long lo, long long hi) { return (int)std::max(lo, std::min(v, hi)); };
