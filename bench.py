@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="blobs", choices=["blobs", "ensemble", "core_shell", "lattice", "uniform"],
+                    help="blobs is the headline; the others measure the remaining configurations")
     return ap.parse_args()
 
 
@@ -203,6 +205,108 @@ def run_reference(args, rank, world):
     return 0
 
 
+# ---------------------------------------------------------------- other workloads
+# algorithmic HBM bytes per agent of the FP32-form iteration, by phase (see
+# the design doc): keys 33, scatter 12, brick sort 56, force 74 (32 for a static
+# agent: its index, flags, contacts and the position read for the bounding box)
+STEP_BYTES_MOVING, STEP_BYTES_STATIC = 33 + 12 + 56 + 74, 33 + 12 + 56 + 32
+
+
+def timed_steps(sim, k, stream):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_other(args):
+    import numpy as np
+    import torch
+
+    from paper_2301_06984_gb300 import bdm
+    from paper_2301_06984_gb300 import workloads as W
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    line = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "data": "synthetic"}
+    if args.workload == "ensemble":
+        w = W.ensemble()
+        sim = bdm.Simulation.from_workload(w)
+        sim.set_workload(w)
+        sim.step(args.warmup)
+        ms = timed_steps(sim, args.steps, stream)
+        line.update(value=w.n * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps, dtype="f32",
+                    config={"workload": "ensemble-512: 512 independent simulations, 10^U[3,5] agents each, "
+                                        "0.25 volume fraction cubes, d = 10 um, dt U[0.005,0.02]; all "
+                                        "simulations in one CUDA-graph launch sequence per iteration",
+                            "n_agents": w.n, "n_sims": w.n_sims})
+        # baseline: one simulation object (own graph) per member, launched one after another
+        sims = []
+        for m in range(w.n_sims):
+            lo, hi = w.sim_off[m], w.sim_off[m + 1]
+            q = bdm.Simulation(R=10.0, capacity=int(hi - lo), dt=float(w.dt_sim[m]), precision="fp32")
+            q.set_agents(w.x[lo:hi], w.y[lo:hi], w.z[lo:hi], w.diam[lo:hi])
+            q.step(args.warmup)
+            sims.append(q)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for q in sims:
+            q.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        line["one_launch_per_simulation"] = {"value": w.n * args.steps / (ms1 * 1e-3), "unit": UNIT,
+                                             "ms_per_step": ms1 / args.steps}
+        line["batched_speedup"] = ms1 / ms
+        for q in sims:
+            q.close()
+    elif args.workload == "core_shell":
+        w = W.core_shell()
+        sim = bdm.Simulation.from_workload(w)
+        sim.set_workload(w)
+        sim.step(args.warmup)
+        c0 = sim.counters()
+        ms = timed_steps(sim, args.steps, stream)
+        c = sim.counters()
+        sim.profile_begin()
+        sim.step(1)
+        phases = sim.profile_end()
+        st = c["n_static"]
+        bytes_step = STEP_BYTES_MOVING * (w.n - st) + STEP_BYTES_STATIC * st
+        peaks = measured_peaks()
+        gbs = bytes_step / (ms / args.steps * 1e-3) / 1e9
+        line.update(value=w.n * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps, dtype="f32",
+                    config={"workload": "core_shell-150M: FCC static core (90%%) + random-walk shell (10%%), "
+                                        "d = 10 um, R = L = 10 um, static-agent skip on", "n_agents": w.n},
+                    skipped_fraction=st / w.n,
+                    roofline={"bound": "hbm", "kernel": "whole iteration", "achieved": gbs,
+                              "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                              "frac": gbs / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+                              "traffic": None, "bytes_per_step_algorithmic": bytes_step},
+                    phases_ms_per_step={k: round(v[0], 4) for k, v in phases.items()},
+                    gpu_launches=c["kernels_launched"] - c0["kernels_launched"])
+    else:
+        w = W.lattice() if args.workload == "lattice" else W.uniform()
+        cap = 4 * w.n + 16 if args.workload == "lattice" else w.n
+        vol = (math.pi / 6.0) * w.diam ** 3 if args.workload == "lattice" else None
+        sim = bdm.Simulation.from_workload(w, capacity=cap)
+        sim.set_agents(w.x, w.y, w.z, w.diam, vol=vol, beh=w.beh)
+        total, tms = 0, 0.0
+        for t in range(w.steps):
+            total += sim.counters()["n_agents"]
+            tms += timed_steps(sim, 1, stream)
+        line.update(value=total / (tms * 1e-3), ms_per_step=tms / w.steps, steps=w.steps, warmup=0, dtype="f64",
+                    config={"workload": w.name + " (FP64 form)", "n_agents_final": sim.counters()["n_agents"]})
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -211,6 +315,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload != "blobs":
+        return run_other(args)
 
     import numpy as np
     import torch

@@ -192,6 +192,29 @@ int bdm_get_counters(bdm_sim *sim, bdm_counters *out);
 #define BDM_DBG_FORCES_NOW 9
 int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out);
 
+/* Autotuner.  Times `trial_steps` iterations of the production path (after
+ * one warm-up iteration) for each candidate setting, restoring the state
+ * before every trial, and keeps the fastest: the box edge L in {R, 1.125 R,
+ * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the lanes per agent of the FP32-force
+ * kernel in {per-box cost model, 1, 2, 4} (BDM_TUNE_LANES), and the sort
+ * cadence in {current, 0, 5, 10, 20} (BDM_TUNE_SORT), one dimension after the
+ * other.  The state (agents, step, uid counter) is the same afterwards; the
+ * static-detection history starts empty.  Changing L keeps neighbour sets
+ * exact (any L >= R does) but changes the FP64 form's canonical summation
+ * order.  Errors: BDM_ESTATE (no agents), BDM_EINVAL, BDM_ENOMEM, BDM_ECUDA. */
+#define BDM_TUNE_BOX_EDGE 1
+#define BDM_TUNE_LANES 2
+#define BDM_TUNE_SORT 4
+typedef struct {
+  double box_edge;     /* chosen L (um)                                     */
+  double ms_per_step;  /* measured time per iteration of the chosen setting */
+  int32_t lanes;       /* 0 = cost model, else fixed lanes per agent        */
+  int32_t sort_every;  /* chosen sort cadence                               */
+  int32_t n_trials;    /* settings timed                                    */
+  int32_t reserved;
+} bdm_tuning;
+int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
+
 /* Phase profiling.  After bdm_profile_begin, bdm_step launches each
  * iteration kernel by kernel (no graph) with a CUDA event before every phase
  * on the simulation's stream; bdm_profile_end waits for the work, writes per

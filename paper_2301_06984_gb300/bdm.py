@@ -41,6 +41,14 @@ class Params(C.Structure):
     ]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("box_edge", C.c_double), ("ms_per_step", C.c_double), ("lanes", C.c_int32),
+                ("sort_every", C.c_int32), ("n_trials", C.c_int32), ("reserved", C.c_int32)]
+
+
+TUNE_BOX_EDGE, TUNE_LANES, TUNE_SORT = 1, 2, 4
+
+
 class Counters(C.Structure):
     _fields_ = [
         ("n_agents", C.c_int64), ("step", C.c_int64), ("next_uid", C.c_uint64), ("n_static", C.c_int64),
@@ -78,6 +86,7 @@ SIGNATURES = {
     "bdm_forces_noalloc": (C.c_int, [C.c_int64, C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double,
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bdm_noalloc_last_error": (C.c_char_p, []),
+    "bdm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Tuning)]),
 }
 
 
@@ -279,6 +288,11 @@ class Simulation:
         self._check(rc)
         return dict(x=xyz[0, :n], y=xyz[1, :n], z=xyz[2, :n], diam=d[:n], vol=v[:n], uid=u[:n], beh=b[:n],
                     sim_off=so, n=nout.value, step=st.value, next_uid=nu.value)
+
+    def autotune(self, trial_steps=3, what=TUNE_BOX_EDGE | TUNE_LANES | TUNE_SORT):
+        t = Tuning()
+        self._check(lib().bdm_autotune(self._h, int(trial_steps), int(what), C.byref(t)))
+        return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
 
     # ------------------------------------------------------------------ profiling
     def profile_begin(self):

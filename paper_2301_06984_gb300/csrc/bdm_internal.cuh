@@ -110,7 +110,7 @@ struct DevParams {
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk;
-  int32_t pad;
+  int32_t lanes_fixed;              // 0: lanes per agent from the per-box cost model
 };
 
 // Everything a kernel reaches, passed by value.

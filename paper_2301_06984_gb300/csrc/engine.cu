@@ -755,6 +755,133 @@ int bdm_get_counters(bdm_sim *s, bdm_counters *out) {
   return BDM_OK;
 }
 
+static int apply_params(bdm_sim *s, const bdm_params &P, int lanes) {
+  s->P = P;
+  DevParams d = make_dev_params(P);
+  d.lanes_fixed = lanes;
+  s->dp = d;
+  if (s->graph_ok) {
+    cudaGraphExecDestroy(s->exec);
+    s->exec = nullptr;
+    s->graph_ok = false;
+  }
+  return BDM_OK;
+}
+
+int bdm_autotune(bdm_sim *s, int trial_steps, int what, bdm_tuning *out) {
+  if (!s || trial_steps < 1) return s ? fail(s, BDM_EINVAL, "trial_steps must be >= 1") : BDM_EINVAL;
+  if (!s->have_agents) return fail(s, BDM_ESTATE, "bdm_set_agents must come first");
+  int rc = read_counters(s);
+  if (rc) return rc;
+  const long long n = s->h_ctr->n;
+  const int64_t step0 = s->h_ctr->step;
+  const uint64_t uid0 = s->h_ctr->next_uid;
+  // snapshot of the state in the layout bdm_set_agents takes
+  const size_t per = 8 * 3 + 8 + 8 + 8 + 1;
+  void *snap = nullptr;
+  if (cudaMalloc(&snap, per * (size_t)std::max<long long>(n, 1) + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(s, BDM_ENOMEM, "autotune snapshot allocation failed");
+  }
+  double *xyz = (double *)snap;
+  double *dia = xyz + 3 * n;
+  double *vol = dia + n;
+  uint64_t *uid = (uint64_t *)(vol + n);
+  uint8_t *beh = (uint8_t *)(uid + n);
+  const bool have_vol = s->sets[0].vol != nullptr;
+  int64_t nn = 0, st = 0;
+  uint64_t nu = 0;
+  rc = bdm_get_agents(s, n, xyz, dia, have_vol ? vol : nullptr, uid, beh, nullptr, &nn, &st, &nu, BDM_DEVICE);
+  std::vector<int64_t> off_h(s->sim_off.begin(), s->sim_off.end());
+  if (s->n_sims == 1) off_h = {0, (int64_t)n};
+  // bdm_set_agents with BDM_DEVICE reads sim_offsets from device memory
+  long long *d_off = nullptr;
+  if (rc == BDM_OK && s->n_sims > 1) {
+    if (cudaMalloc(&d_off, sizeof(long long) * (s->n_sims + 1)) != cudaSuccess ||
+        cudaMemcpy(d_off, off_h.data(), sizeof(long long) * (s->n_sims + 1), cudaMemcpyHostToDevice) != cudaSuccess) {
+      cudaGetLastError();
+      rc = fail(s, BDM_ENOMEM, "autotune offsets allocation failed");
+    }
+  }
+  auto restore_dev = [&]() {
+    return bdm_set_agents(s, n, xyz, dia, have_vol ? vol : nullptr, uid, beh, (const int64_t *)d_off, step0, uid0,
+                          BDM_DEVICE);
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == BDM_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) {
+    cudaGetLastError();
+    rc = fail(s, BDM_ECUDA, "autotune events");
+  }
+  const bdm_params base = s->P;
+  const double R = base.interaction_radius;
+  bdm_params best = base;
+  int best_lanes = s->dp.lanes_fixed;
+  double best_ms = 1e300;
+  int trials = 0;
+  auto trial = [&](const bdm_params &P, int lanes, double *ms) -> int {
+    int r = apply_params(s, P, lanes);
+    if (r) return r;
+    if ((r = restore_dev())) return r;
+    if ((r = bdm_step(s, 1))) return r;
+    CK(cudaEventRecord(e0, s->own));
+    if ((r = bdm_step(s, trial_steps))) return r;
+    CK(cudaEventRecord(e1, s->own));
+    CK(cudaEventSynchronize(e1));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, e0, e1));
+    *ms = t / trial_steps;
+    trials++;
+    return BDM_OK;
+  };
+  if (rc == BDM_OK) {
+    double ms = 0;
+    rc = trial(best, best_lanes, &best_ms);
+    if (rc == BDM_OK && (what & BDM_TUNE_BOX_EDGE)) {
+      const double f[4] = {1.0, 1.125, 1.25, 1.5};
+      bdm_params b = best;
+      for (int i = 0; i < 4 && rc == BDM_OK; ++i) {
+        bdm_params P = b;
+        P.box_edge = R * f[i];
+        if ((rc = trial(P, best_lanes, &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; best = P; }
+      }
+    }
+    if (rc == BDM_OK && (what & BDM_TUNE_LANES) && base.precision == BDM_FP32_FORCE) {
+      const int opts[4] = {0, 1, 2, 4};
+      int bl = best_lanes;
+      for (int i = 0; i < 4 && rc == BDM_OK; ++i)
+        if ((rc = trial(best, opts[i], &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; bl = opts[i]; }
+      best_lanes = bl;
+    }
+    if (rc == BDM_OK && (what & BDM_TUNE_SORT)) {
+      const int opts[4] = {0, 5, 10, 20};
+      bdm_params b = best;
+      for (int i = 0; i < 4 && rc == BDM_OK; ++i) {
+        bdm_params P = b;
+        P.sort_every = opts[i];
+        if ((rc = trial(P, best_lanes, &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; best = P; }
+      }
+    }
+  }
+  // keep the best setting and the original state
+  int rc2 = apply_params(s, best, best_lanes);
+  if (rc2 == BDM_OK) rc2 = restore_dev();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (d_off) cudaFree(d_off);
+  cudaFree(snap);
+  if (rc) return rc;
+  if (rc2) return rc2;
+  if (out) {
+    out->box_edge = best.box_edge > 0.0 ? best.box_edge : R;
+    out->ms_per_step = best_ms;
+    out->lanes = best_lanes;
+    out->sort_every = best.sort_every;
+    out->n_trials = trials;
+    out->reserved = 0;
+  }
+  return BDM_OK;
+}
+
 int bdm_profile_begin(bdm_sim *s) {
   if (!s) return BDM_EINVAL;
   s->prof_on = true;

@@ -216,19 +216,35 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 }
 
 #define FORCE_WARPS 8
-#define QCAP 32
+#define CHUNK 96
+
+// flush a warp's shared bounding-box accumulator into the simulation's
+__device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParams &P, int nxt, int sim,
+                                                unsigned long long *bb_w) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0 && sim >= 0 && bb_w[0] != ~0ull) {
+    unsigned long long *bb = B.bbox + ((size_t)nxt * P.n_sims + sim) * 6;
+    for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], bb_w[d]); atomicMax(&bb[3 + d], bb_w[3 + d]); }
+  }
+  __syncwarp();
+  if ((threadIdx.x & 31) < 6) bb_w[threadIdx.x & 31] = ((threadIdx.x & 31) < 3) ? ~0ull : 0ull;
+  __syncwarp();
+}
 
 template <int PREC, int MODE>
-__global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevParams P) {
+__global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevParams P) {
   __shared__ int s_nocc[27];
   __shared__ unsigned long long s_ndirty[27];
   __shared__ int s_next;
   __shared__ long long s_o;
   __shared__ float4 s_off[27];
-  // per-lane queues of candidates that passed the FP32 prefilter:
-  // [warp][slot][lane], so every lane writes its own bank
-  __shared__ uint32_t s_q[FORCE_WARPS][QCAP][32];
-  __shared__ uint8_t s_qk[FORCE_WARPS][QCAP][32];
+  __shared__ unsigned long long s_bb[FORCE_WARPS][6];
+  // per warp: a staged chunk of candidate records (box offset applied) and
+  // their sorted positions, and per-lane queues of the chunk entries that
+  // passed the FP32 prefilter ([warp][slot][lane]: each lane its own bank)
+  __shared__ float4 s_c[FORCE_WARPS][CHUNK];
+  __shared__ uint32_t s_kj[FORCE_WARPS][CHUNK];
+  __shared__ uint8_t s_q[FORCE_WARPS][CHUNK][32];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
@@ -237,13 +253,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevPar
   const long long n_occ = C->n_occ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long step = C->step;
-  unsigned long long c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
+  unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
   int wsim = -1;
-  unsigned long long bmin[3] = {~0ull, ~0ull, ~0ull}, bmax[3] = {0ull, 0ull, 0ull};
   if (threadIdx.x < 27) {
     const int t = threadIdx.x;
     s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
   }
+  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
 
   while (true) {
     __syncthreads();
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevPar
     }
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
-      flush_bbox(B, P, nxt, wsim, bmin, bmax);
+      flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
     const double dt = G.dt;
@@ -303,7 +319,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevPar
       const bool clean = !__any_sync(0xffffffffu, nb_dirty);
       // lanes per agent: split the candidates of small boxes over several lanes
       int S = 1;
-      if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
+      if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES) && P.lanes_fixed > 0) {
+        S = P.lanes_fixed;
+      } else if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
         unsigned ctot = nb_cnt;
         for (int of = 16; of > 0; of >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, of);
         unsigned best = 0xffffffffu;
@@ -332,175 +350,178 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevPar
         unsigned ncont = 0, nnb = 0;
         long long lbase = 0;
         if (MODE == FM_LIST_NBR && valid) lbase = B.nbr_off[iq];
-        if (__any_sync(0xffffffffu, compute)) {
-          unsigned qlen = 0;
-          // evaluate the queued pairs with every lane busy; the queue keeps
-          // each lane's candidate order, so the FP64 form keeps the
-          // canonical summation order
-          auto drain = [&]() {
-            const unsigned mx = __reduce_max_sync(0xffffffffu, qlen);
-            for (unsigned m = 0; m < mx; ++m) {
-              if (m >= qlen) continue;
-              const unsigned kj = s_q[warp][m][lane];
-              if (PREC == 0) {
-                const dbl4 cj = B.c64[kj];
+        bool refine = false;
+        double hx = 0.0, hy = 0.0, hz = 0.0;
+        for (int pass = 0; pass < 2; ++pass) {
+          const bool act = (pass == 0) ? compute : refine;
+          if (__any_sync(0xffffffffu, act)) {
+            // The warp stages its stencil's candidates in chunks of CHUNK
+            // records in shared memory (coalesced copies, neighbour-box offset
+            // applied once), every lane tests its share of the chunk in FP32
+            // and queues the ones that may be neighbours, then the queued pairs
+            // are evaluated with every lane busy.  Chunks follow the canonical
+            // order and queues keep each lane's order, so the FP64 form keeps
+            // the canonical summation order.
+            float4 *const sc = s_c[warp];
+            uint32_t *const skj = s_kj[warp];
+            int k = -1;
+            unsigned st = 0, cnt = 0, base = 0;
+            float4 of = make_float4(0.f, 0.f, 0.f, 0.f);
+            while (true) {
+              // ---- stage the next chunk
+              unsigned fill = 0;
+              while (fill < CHUNK) {
+                if (base >= cnt) {
+                  if (++k >= 27) break;
+                  st = __shfl_sync(0xffffffffu, nb_st, k);
+                  cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
+                  base = 0;
+                  of = s_off[k];
+                  continue;
+                }
+                const unsigned take = min(cnt - base, CHUNK - fill);
+                for (unsigned t = lane; t < take; t += 32) {
+                  const float4 c = __ldg(&B.c32[st + base + t]);
+                  sc[fill + t] = make_float4(c.x + of.x, c.y + of.y, c.z + of.z, c.w);
+                  skj[fill + t] = st + base + t;
+                }
+                fill += take;
+                base += take;
+              }
+              if (fill == 0) break;
+              __syncwarp();
+              // ---- test the chunk in FP32, queue the candidates inside the band
+              unsigned qlen = 0;
+              if (act) {
+                for (unsigned i = sub; i < fill; i += S) {
+                  const float4 c = sc[i];
+                  const float ex = cq.x - c.x, ey = cq.y - c.y, ez = cq.z - c.z;
+                  const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  if (d2 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)i;
+                }
+                if (pass == 0) c_cand += (fill > (unsigned)sub) ? (fill - sub + S - 1) / S : 0u;
+              }
+              // ---- evaluate the queued pairs
+              const unsigned mx = __reduce_max_sync(0xffffffffu, qlen);
+              for (unsigned m = 0; m < mx; ++m) {
+                if (m >= qlen) continue;
+                const unsigned i = s_q[warp][m][lane];
+                const unsigned kj = skj[i];
+                if (kj == kq) continue;  // the agent itself
+                if (PREC == 0) {
+                  const dbl4 cj = B.c64[kj];
+                  if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
+                    if (is_nbr_f64(P, dq, cj)) {
+                      if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
+                      nnb++;
+                    }
+                    continue;
+                  }
+                  const int r = pair_f64(P, dq, cj, dfx, dfy, dfz);
+                  nnb += (r > 0);
+                  ncont += (r == 2);
+                  continue;
+                }
+                const float4 c = sc[i];
+                const float ex = cq.x - c.x, ey = cq.y - c.y, ez = cq.z - c.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
-                  if (is_nbr_f64(P, dq, cj)) {
+                  bool isn = true;
+                  if (band && d2 > P.R2_lo_f) {
+                    c_exact++;
+                    isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
+                  }
+                  if (isn) {
                     if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
                     nnb++;
                   }
                   continue;
                 }
-                const int r = pair_f64(P, dq, cj, dfx, dfy, dfz);
-                nnb += (r > 0);
-                ncont += (r == 2);
-                continue;
-              }
-              const float4 of = s_off[s_qk[warp][m][lane]];
-              const float4 c = __ldg(&B.c32[kj]);
-              const float ex = (cq.x - of.x) - c.x, ey = (cq.y - of.y) - c.y, ez = (cq.z - of.z) - c.z;
-              const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-              const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
-              if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
-                bool isn = true;
-                if (band && d2 > P.R2_lo_f) {
-                  c_exact++;
-                  isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
-                }
-                if (isn) {
-                  if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
-                  nnb++;
-                }
-                continue;
-              }
-              if (band) {
-                c_exact++;
-                double gx = 0.0, gy = 0.0, gz = 0.0;
-                const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
-                nnb += (r > 0);
-                if (r == 2) {
-                  ncont++;
-                  ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
-                }
-                continue;
-              }
-              nnb++;
-              const float s = cq.w + c.w, s2 = s * s;
-              const float W = fmaf(s, P.cband1, s2 * P.cband2);
-              if (d2 >= s2 + W) continue;  // certainly no contact
-              if (d2 > s2 - W) {           // contact decided in FP64
-                c_exact++;
-                double gx = 0.0, gy = 0.0, gz = 0.0;
-                const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
-                if (r == 2) {
-                  ncont++;
-                  ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
-                }
-                continue;
-              }
-              const float inv_d = rsqrtf(d2);
-              const float d = d2 * inv_d;
-              const float delta = s - d;
-              const float rbar = __fdividef(cq.w * c.w, s);
-              const float sq = sqrtf(rbar * delta);
-              const float kd = P.kf * delta, gs = P.gammaf * sq;
-              const float sc = (kd - gs) * inv_d;
-              if (delta < P.graze) {
-                // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
-                // so keep it apart with a bound of its FP32 error
-                gfx = fmaf(sc, ex, gfx);
-                gfy = fmaf(sc, ey, gfy);
-                gfz = fmaf(sc, ez, gfz);
-                gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
-                                                P.gammaf * sqrtf(rbar * P.graze_e))
-                                        : P.gammaf * sqrtf(rbar * P.graze_e);
-              } else {
-                ffx = fmaf(sc, ex, ffx);
-                ffy = fmaf(sc, ey, ffy);
-                ffz = fmaf(sc, ez, ffz);
-              }
-              fscale += kd + gs;
-              ncont++;
-            }
-            qlen = 0;
-            __syncwarp();
-          };
-          for (int k = 0; k < 27; ++k) {
-            const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
-            if (cnt == 0) continue;
-            const float4 of = s_off[k];
-            const float xq = cq.x - of.x, yq = cq.y - of.y, zq = cq.z - of.z;
-            for (unsigned jj = 0; jj < cnt; jj += S) {
-              const unsigned j = jj + sub;
-              const unsigned kj = st + j;
-              bool hit = false;
-              if (compute && j < cnt) {
-                const float4 c = __ldg(&B.c32[kj]);
-                const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                c_cand++;
-                hit = (d2 < P.R2_hi_f) && (kj != kq);
-              }
-              if (hit) {
-                s_q[warp][qlen][lane] = kj;
-                s_qk[warp][qlen][lane] = (uint8_t)k;
-                ++qlen;
-              }
-              if (__any_sync(0xffffffffu, qlen == QCAP)) drain();
-            }
-          }
-          if (__any_sync(0xffffffffu, qlen > 0)) drain();
-        }
-        // reduce the S partial sums of an agent
-        for (int of = S >> 1; of > 0; of >>= 1) {
-          ffx += __shfl_xor_sync(0xffffffffu, ffx, of);
-          ffy += __shfl_xor_sync(0xffffffffu, ffy, of);
-          ffz += __shfl_xor_sync(0xffffffffu, ffz, of);
-          ncont += __shfl_xor_sync(0xffffffffu, ncont, of);
-          nnb += __shfl_xor_sync(0xffffffffu, nnb, of);
-          if (PREC == 1) {
-            gfx += __shfl_xor_sync(0xffffffffu, gfx, of);
-            gfy += __shfl_xor_sync(0xffffffffu, gfy, of);
-            gfz += __shfl_xor_sync(0xffffffffu, gfz, of);
-            gbound += __shfl_xor_sync(0xffffffffu, gbound, of);
-            fscale += __shfl_xor_sync(0xffffffffu, fscale, of);
-          }
-        }
-        if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
-          // accept the grazing sum when its error bound is a small part of the
-          // agent's tolerance; otherwise redo those pairs in FP64
-          const bool refine = compute && gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol);
-          if (__any_sync(0xffffffffu, refine)) {
-            double hx = 0.0, hy = 0.0, hz = 0.0;
-            for (int k = 0; k < 27; ++k) {
-              const unsigned st = __shfl_sync(0xffffffffu, nb_st, k), cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
-              if (cnt == 0) continue;
-              const float ox = (float)(k % 3 - 1) * P.Lf, oy = (float)((k / 3) % 3 - 1) * P.Lf,
-                          oz = (float)(k / 9 - 1) * P.Lf;
-              const float xq = cq.x - ox, yq = cq.y - oy, zq = cq.z - oz;
-              for (unsigned j = sub; j < cnt; j += S) {
-                if (!refine) continue;
-                const unsigned kj = st + j;
-                const float4 c = __ldg(&B.c32[kj]);
-                const float ex = xq - c.x, ey = yq - c.y, ez = zq - c.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                if (d2 >= P.R2_hi_f || kj == kq || d2 > P.R2_lo_f || d2 < TINY2) continue;
                 const float s = cq.w + c.w, s2 = s * s;
                 const float W = fmaf(s, P.cband1, s2 * P.cband2);
-                if (d2 >= s2 + W || d2 > s2 - W) continue;
-                const float delta = s - d2 * rsqrtf(d2);
-                if (!(delta < P.graze)) continue;
-                c_exact++;
-                pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
+                if (pass == 1 && (band || d2 > s2 - W)) continue;  // not an FP32 contact
+                if (band || (d2 > s2 - W && d2 < s2 + W)) {
+                  // cutoff or contact decided in FP64
+                  c_exact++;
+                  double gx = 0.0, gy = 0.0, gz = 0.0;
+                  const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                  nnb += (r > 0);
+                  if (r == 2) {
+                    ncont++;
+                    ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
+                  }
+                  continue;
+                }
+                if (pass == 0) nnb++;
+                if (d2 >= s2 + W) continue;  // certainly no contact
+                const float inv_d = rsqrtf(d2);
+                const float d = d2 * inv_d;
+                const float delta = s - d;
+                const float rbar = __fdividef(cq.w * c.w, s);
+                const float sq = sqrtf(rbar * delta);
+                const float kd = P.kf * delta, gs = P.gammaf * sq;
+                const float scf = (kd - gs) * inv_d;
+                if (pass == 1) {
+                  // refinement: the grazing contacts of pass 0, classified by the
+                  // same FP32 arithmetic, redone in FP64
+                  if (delta < P.graze) {
+                    c_exact++;
+                    pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
+                  }
+                  continue;
+                }
+                if (delta < P.graze) {
+                  // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
+                  // so keep it apart with a bound of its FP32 error
+                  gfx = fmaf(scf, ex, gfx);
+                  gfy = fmaf(scf, ey, gfy);
+                  gfz = fmaf(scf, ez, gfz);
+                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
+                                                  P.gammaf * sqrtf(rbar * P.graze_e))
+                                          : P.gammaf * sqrtf(rbar * P.graze_e);
+                } else {
+                  ffx = fmaf(scf, ex, ffx);
+                  ffy = fmaf(scf, ey, ffy);
+                  ffz = fmaf(scf, ez, ffz);
+                }
+                fscale += kd + gs;
+                ncont++;
               }
+              __syncwarp();
             }
+          }
+          if (pass == 1) {
             for (int of = S >> 1; of > 0; of >>= 1) {
               hx += __shfl_xor_sync(0xffffffffu, hx, of);
               hy += __shfl_xor_sync(0xffffffffu, hy, of);
               hz += __shfl_xor_sync(0xffffffffu, hz, of);
             }
             if (refine) { gfx = (float)hx; gfy = (float)hy; gfz = (float)hz; }
+            break;
           }
+          // reduce the S partial sums of an agent
+          for (int of = S >> 1; of > 0; of >>= 1) {
+            ffx += __shfl_xor_sync(0xffffffffu, ffx, of);
+            ffy += __shfl_xor_sync(0xffffffffu, ffy, of);
+            ffz += __shfl_xor_sync(0xffffffffu, ffz, of);
+            ncont += __shfl_xor_sync(0xffffffffu, ncont, of);
+            nnb += __shfl_xor_sync(0xffffffffu, nnb, of);
+            if (PREC == 1) {
+              gfx += __shfl_xor_sync(0xffffffffu, gfx, of);
+              gfy += __shfl_xor_sync(0xffffffffu, gfy, of);
+              gfz += __shfl_xor_sync(0xffffffffu, gfz, of);
+              gbound += __shfl_xor_sync(0xffffffffu, gbound, of);
+              fscale += __shfl_xor_sync(0xffffffffu, fscale, of);
+            }
+          }
+          if (PREC != 1 || !(MODE == FM_STEP || MODE == FM_FORCES)) break;
+          // accept the grazing sum when its error bound is a small part of the
+          // agent's tolerance; otherwise redo those pairs in FP64 (pass 1)
+          refine = compute && gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol);
+          if (!__any_sync(0xffffffffu, refine)) break;
+        }
+        if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
           ffx += gfx;
           ffy += gfy;
           ffz += gfz;
@@ -615,27 +636,25 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 3) k_force(DevBufs B, DevPar
         }
         A.flags[iq] = nfl;
         if (P.keep_forces) { B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz; }
-        const unsigned long long e0 = enc_f64(nx), e1 = enc_f64(ny), e2 = enc_f64(nzp);
-        bmin[0] = min(bmin[0], e0); bmax[0] = max(bmax[0], e0);
-        bmin[1] = min(bmin[1], e1); bmax[1] = max(bmax[1], e1);
-        bmin[2] = min(bmin[2], e2); bmax[2] = max(bmax[2], e2);
+        atomicMin(&s_bb[warp][0], enc_f64(nx));
+        atomicMax(&s_bb[warp][3], enc_f64(nx));
+        atomicMin(&s_bb[warp][1], enc_f64(ny));
+        atomicMax(&s_bb[warp][4], enc_f64(ny));
+        atomicMin(&s_bb[warp][2], enc_f64(nzp));
+        atomicMax(&s_bb[warp][5], enc_f64(nzp));
       }
     }
   }
-  if (MODE == FM_STEP) flush_bbox(B, P, nxt, wsim, bmin, bmax);
-  c_static = wsum64(c_static);
-  c_moved = wsum64(c_moved);
-  c_cand = wsum64(c_cand);
-  c_nbr = wsum64(c_nbr);
-  c_cont = wsum64(c_cont);
-  c_exact = wsum64(c_exact);
+  if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = wsum64(c_cand),
+                           t_nbr = wsum64(c_nbr), t_cont = wsum64(c_cont), t_exact = wsum64(c_exact);
   if (lane == 0) {
-    if (c_static) atomicAdd(&C->a_static, c_static);
-    if (c_moved) atomicAdd(&C->a_moved, c_moved);
-    if (c_cand) atomicAdd(&C->a_cand, c_cand);
-    if (c_nbr) atomicAdd(&C->a_nbr, c_nbr);
-    if (c_cont) atomicAdd(&C->a_contact, c_cont);
-    if (c_exact) atomicAdd(&C->a_exact, c_exact);
+    if (t_static) atomicAdd(&C->a_static, t_static);
+    if (t_moved) atomicAdd(&C->a_moved, t_moved);
+    if (t_cand) atomicAdd(&C->a_cand, t_cand);
+    if (t_nbr) atomicAdd(&C->a_nbr, t_nbr);
+    if (t_cont) atomicAdd(&C->a_contact, t_cont);
+    if (t_exact) atomicAdd(&C->a_exact, t_exact);
   }
 }
 

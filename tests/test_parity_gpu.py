@@ -339,3 +339,35 @@ def test_grid_capacity_grows_transparently():
     pos, _ = H.gpu_positions(s)
     assert np.array_equal(pos, o.positions())
     assert s.counters()["n_bricks"] > (1 << 16)
+
+
+# ------------------------------------------------------------------ autotuner
+def test_autotune_fp64_keeps_state_and_stays_bit_exact():
+    w = W.uniform(n=8192, seed=11)
+    s = H.gpu_sim(w, precision="fp64")
+    s.step(2)
+    before, a0 = H.gpu_positions(s)
+    t = s.autotune(trial_steps=2, what=bdm.TUNE_BOX_EDGE | bdm.TUNE_SORT)
+    after, a1 = H.gpu_positions(s)
+    assert np.array_equal(before, after) and a1["step"] == a0["step"] == 2
+    assert t["box_edge"] in (12.0, 13.5, 15.0, 18.0) and t["sort_every"] in (0, 5, 10, 20)
+    assert t["n_trials"] >= 9
+    o = O.State(a1["x"], a1["y"], a1["z"], a1["diam"], uid=a1["uid"], step=2)
+    s.step(4)
+    o.step(H.oracle_params(w, L=t["box_edge"], sort_every=t["sort_every"]), 4)
+    pos, a = H.gpu_positions(s)
+    assert np.array_equal(a["uid"], o.uid[: o.n])
+    assert np.array_equal(pos, o.positions())
+
+
+def test_autotune_fp32_lanes_keep_tolerance():
+    w = H.small_blobs(n=40_000, seed=13)
+    s = H.gpu_sim(w)
+    t = s.autotune(trial_steps=2)
+    assert t["lanes"] in (0, 1, 2, 4)
+    f_g, nz_g, nnb_g = s.forces_now()
+    a = s.get_agents()
+    o = O.State(a["x"], a["y"], a["z"], a["diam"])
+    f_o, nz_o, nnb_o, scale = o.forces_of(H.oracle_params(w, L=t["box_edge"]), with_scale=True)
+    assert np.array_equal(nnb_g, nnb_o) and np.array_equal(nz_g, nz_o)
+    H.assert_fp32_forces(f_g, f_o, scale)
