@@ -245,6 +245,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ float4 s_c[FORCE_WARPS][CHUNK];
   __shared__ uint32_t s_kj[FORCE_WARPS][CHUNK];
   __shared__ uint8_t s_q[FORCE_WARPS][CHUNK][32];
+  __shared__ unsigned s_pre[FORCE_WARPS][28], s_st[FORCE_WARPS][28];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
@@ -261,6 +262,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   }
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
 
+  // One block per occupied brick (taken from a global counter); its warps
+  // take the brick's 64 boxes from a block counter.
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -317,18 +320,28 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
       }
       const bool clean = !__any_sync(0xffffffffu, nb_dirty);
+      // exclusive prefix of the stencil box counts (canonical box order)
+      unsigned pre = nb_cnt;
+      for (int of = 1; of < 32; of <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
+        if (lane >= of) pre += y;
+      }
+      const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
+      if (lane < 27) {
+        s_pre[warp][lane] = pre - nb_cnt;
+        s_st[warp][lane] = nb_st;
+      }
+      __syncwarp();
       // lanes per agent: split the candidates of small boxes over several lanes
       int S = 1;
       if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES) && P.lanes_fixed > 0) {
         S = P.lanes_fixed;
       } else if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
-        unsigned ctot = nb_cnt;
-        for (int of = 16; of > 0; of >>= 1) ctot += __shfl_xor_sync(0xffffffffu, ctot, of);
         unsigned best = 0xffffffffu;
-        for (int sl = 1; sl <= 32; sl <<= 1) {
-          const unsigned g = 32u / sl;
-          const unsigned cost = ((nq + g - 1) / g) * ((ctot + sl - 1) / sl + 2u);
-          if (cost < best) { best = cost; S = sl; }
+        for (int ls = 0; ls <= 5; ++ls) {
+          const unsigned passes = (nq + (32u >> ls) - 1) >> (5 - ls);
+          const unsigned cost = passes * (((ctot + (1u << ls) - 1) >> ls) + 2u);
+          if (cost < best) { best = cost; S = 1 << ls; }
         }
       }
       const int sub = lane & (S - 1);
@@ -364,36 +377,65 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
             // the canonical summation order.
             float4 *const sc = s_c[warp];
             uint32_t *const skj = s_kj[warp];
-            int k = -1;
-            unsigned st = 0, cnt = 0, base = 0;
-            float4 of = make_float4(0.f, 0.f, 0.f, 0.f);
+            unsigned c0 = 0;
             while (true) {
-              // ---- stage the next chunk
-              unsigned fill = 0;
-              while (fill < CHUNK) {
-                if (base >= cnt) {
-                  if (++k >= 27) break;
-                  st = __shfl_sync(0xffffffffu, nb_st, k);
-                  cnt = __shfl_sync(0xffffffffu, nb_cnt, k);
-                  base = 0;
-                  of = s_off[k];
-                  continue;
-                }
-                const unsigned take = min(cnt - base, CHUNK - fill);
-                for (unsigned t = lane; t < take; t += 32) {
-                  const float4 c = __ldg(&B.c32[st + base + t]);
-                  sc[fill + t] = make_float4(c.x + of.x, c.y + of.y, c.z + of.z, c.w);
-                  skj[fill + t] = st + base + t;
-                }
-                fill += take;
-                base += take;
+              // ---- stage the next chunk: every lane locates its positions in
+              // the stencil (binary search over the box prefix sums), so all
+              // loads of a chunk are independent and in flight together
+              const unsigned fill = (c0 < ctot) ? min((unsigned)CHUNK, ctot - c0) : 0u;
+              constexpr int PER_LANE = (CHUNK + 31) / 32;
+              unsigned kjs[PER_LANE];
+              int boxs[PER_LANE];
+#pragma unroll
+              for (int m = 0; m < PER_LANE; ++m) {
+                // branch-free binary search: last stencil box starting at or
+                // before this chunk position (empty boxes are skipped because
+                // the next box starts at the same position)
+                const unsigned p = c0 + lane + 32u * m;
+                int lo = 0;
+#pragma unroll
+                for (int step = 16; step > 0; step >>= 1)
+                  if (lo + step <= 26 && s_pre[warp][lo + step] <= p) lo += step;
+                boxs[m] = lo;
+                kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
               }
+              float4 cs[PER_LANE];
+#pragma unroll
+              for (int m = 0; m < PER_LANE; ++m)
+                if (lane + 32u * m < fill) cs[m] = __ldg(&B.c32[kjs[m]]);
+#pragma unroll
+              for (int m = 0; m < PER_LANE; ++m) {
+                const unsigned t = lane + 32u * m;
+                if (t < fill) {
+                  const float4 of = s_off[boxs[m]];
+                  sc[t] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
+                  skj[t] = kjs[m];
+                }
+              }
+              c0 += fill;
               if (fill == 0) break;
               __syncwarp();
               // ---- test the chunk in FP32, queue the candidates inside the band
               unsigned qlen = 0;
               if (act) {
-                for (unsigned i = sub; i < fill; i += S) {
+                // four independent candidates per iteration (latency hiding)
+                unsigned i = sub;
+                for (; i + 3u * S < fill; i += 4u * S) {
+                  const float4 c0 = sc[i], c1 = sc[i + S], c2 = sc[i + 2 * S], c3 = sc[i + 3 * S];
+                  float ex = cq.x - c0.x, ey = cq.y - c0.y, ez = cq.z - c0.z;
+                  const float e0 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  ex = cq.x - c1.x; ey = cq.y - c1.y; ez = cq.z - c1.z;
+                  const float e1 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  ex = cq.x - c2.x; ey = cq.y - c2.y; ez = cq.z - c2.z;
+                  const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  ex = cq.x - c3.x; ey = cq.y - c3.y; ez = cq.z - c3.z;
+                  const float e3 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  if (e0 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)i;
+                  if (e1 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + S);
+                  if (e2 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + 2 * S);
+                  if (e3 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + 3 * S);
+                }
+                for (; i < fill; i += S) {
                   const float4 c = sc[i];
                   const float ex = cq.x - c.x, ey = cq.y - c.y, ez = cq.z - c.z;
                   const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
@@ -459,7 +501,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 const float d = d2 * inv_d;
                 const float delta = s - d;
                 const float rbar = __fdividef(cq.w * c.w, s);
-                const float sq = sqrtf(rbar * delta);
+                const float rd = rbar * delta;            // > 0: a certain contact
+                const float sq = rd * rsqrtf(rd);
                 const float kd = P.kf * delta, gs = P.gammaf * sq;
                 const float scf = (kd - gs) * inv_d;
                 if (pass == 1) {
@@ -477,7 +520,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   gfx = fmaf(scf, ex, gfx);
                   gfy = fmaf(scf, ey, gfy);
                   gfz = fmaf(scf, ez, gfz);
-                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f / sq,
+                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
                                                   P.gammaf * sqrtf(rbar * P.graze_e))
                                           : P.gammaf * sqrtf(rbar * P.graze_e);
                 } else {
