@@ -140,6 +140,8 @@ struct DevBufs {
   long long *nbr_off;
   long long *nbr_out;
   int32_t *dbg_i32;               // debug: contacts / neighbours
+  float4 *defer_c;                // FP32-form deferred pairs: contribution, bound
+  uint2 *defer_w;                 // FP32-form deferred pairs: index, agent | kind
   long long brick_cap, occ_cap, cap, nbr_cap;
 };
 
@@ -235,8 +237,15 @@ struct LaunchCfg {
   int scan_blocks;    // ceil(brick_cap / SCAN_TILE)
   int agent_scan_blocks;
   int occ_blocks;
-  int force_blocks;
+  int force_blocks;    // k_force (FP64 form, neighbour modes, fixed lanes per agent)
+  int force32_blocks;  // k_force32 (FP32 form)
 };
+
+// the FP32 form's pair-ring force kernel: resident CTAs per SM, warps per
+// CTA, and capacity of each warp's deferred-pair list (global memory)
+constexpr int FORCE32_CTAS_PER_SM = 2;
+#define FORCE32_WARPS 8
+#define FORCE32_DCAP 512
 
 #define SCAN_TILE 2048
 #define SCAN_THREADS 256

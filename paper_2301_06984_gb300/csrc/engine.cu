@@ -178,6 +178,7 @@ static void make_launch_cfg(bdm_sim *s) {
   s->lc.agent_scan_blocks = clampb((s->cap + SCAN_TILE - 1) / SCAN_TILE, 1, 1LL << 30);
   s->lc.occ_blocks = clampb(s->B.occ_cap, 1, sm * 4);
   s->lc.force_blocks = clampb(s->B.occ_cap, 1, sm * 4);
+  s->lc.force32_blocks = clampb(s->B.occ_cap, 1, sm * FORCE32_CTAS_PER_SM);
 }
 
 static int alloc_grid(bdm_sim *s, long long brick_cap, long long occ_cap) {
@@ -248,6 +249,15 @@ static int alloc_agents(bdm_sim *s) {
   A((void **)&B.c32, sizeof(float4) * cap);
   if (f64) A((void **)&B.c64, sizeof(dbl4) * cap);
   else B.c64 = nullptr;
+  if (!f64) {
+    // one deferred-pair list per warp of the FP32 force kernel's grid
+    const size_t nd = (size_t)s->sm_count * FORCE32_CTAS_PER_SM * FORCE32_WARPS * FORCE32_DCAP;
+    A((void **)&B.defer_c, sizeof(float4) * nd);
+    A((void **)&B.defer_w, sizeof(uint2) * nd);
+  } else {
+    B.defer_c = nullptr;
+    B.defer_w = nullptr;
+  }
   if (grow) {
     A((void **)&B.stash, sizeof(dbl4) * cap);
   } else {

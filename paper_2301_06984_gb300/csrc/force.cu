@@ -161,22 +161,26 @@ __device__ __forceinline__ dbl4 exact_of(const DevBufs &B, const AgentSet &A, in
 
 // FP64 pair: returns 0 not a neighbour, 1 neighbour without force, 2 contact
 // (force added to f*)
-__device__ __forceinline__ int pair_f64(const DevParams &P, const dbl4 &q, const dbl4 &c, double &fx, double &fy,
-                                        double &fz) {
+__device__ __forceinline__ int pair_f64_k(double R2, double k, double gamma, const dbl4 &q, const dbl4 &c, double &fx,
+                                          double &fy, double &fz) {
   const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
-  if (!(d2 < P.R2)) return 0;
+  if (!(d2 < R2)) return 0;
   if (d2 == 0.0) return 1;
   const double d = __dsqrt_rn(d2);
   const double delta = __dsub_rn(__dadd_rn(q.w, c.w), d);
   if (!(delta > 0.0)) return 1;
   const double rbar = __ddiv_rn(__dmul_rn(q.w, c.w), __dadd_rn(q.w, c.w));
-  const double F = __dsub_rn(__dmul_rn(P.k, delta), __dmul_rn(P.gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
+  const double F = __dsub_rn(__dmul_rn(k, delta), __dmul_rn(gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
   const double sc = __ddiv_rn(F, d);
   fx = __dadd_rn(fx, __dmul_rn(sc, ddx));
   fy = __dadd_rn(fy, __dmul_rn(sc, ddy));
   fz = __dadd_rn(fz, __dmul_rn(sc, ddz));
   return 2;
+}
+__device__ __forceinline__ int pair_f64(const DevParams &P, const dbl4 &q, const dbl4 &c, double &fx, double &fy,
+                                        double &fz) {
+  return pair_f64_k(P.R2, P.k, P.gamma, q, c, fx, fy, fz);
 }
 
 __device__ __forceinline__ bool is_nbr_f64(const DevParams &P, const dbl4 &q, const dbl4 &c) {
@@ -231,6 +235,130 @@ __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParam
   __syncwarp();
 }
 
+// Per-agent end of the force kernels.  FM_FORCES records the summed force
+// and the contact and neighbour counts in the debug buffers.  FM_STEP forms
+// the displacement (Sec. 5: dt F unless |F| <= adherence, clamped to the
+// maximum displacement, random walk added after the clamp), grows and divides
+// (FP64 form), writes the new position when it or the previous one moved,
+// and records the flags and the simulation's bounding box.
+template <int PREC, int MODE>
+__device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, int nxt,
+                                             long long step, double dt, float dt_f, uint32_t iq, uint8_t fl,
+                                             bool is_static, float ffx, float ffy, float ffz, double dfx, double dfy,
+                                             double dfz, unsigned nnb, unsigned ncont, unsigned &c_static,
+                                             unsigned &c_moved, unsigned long long *bb_w) {
+  double Fx, Fy, Fz;
+  if (PREC == 0) { Fx = dfx; Fy = dfy; Fz = dfz; }
+  else { Fx = ftod_exact(ffx); Fy = ftod_exact(ffy); Fz = ftod_exact(ffz); }
+  if (MODE == FM_FORCES) {
+    B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz;
+    B.dbg_i32[iq] = (int32_t)ncont;
+    B.dbg_i32[B.cap + iq] = (int32_t)nnb;
+    return;
+  }
+  // ----------------------------------------------------- FM_STEP epilogue
+  const double px = A.x[cur][iq], py = A.y[cur][iq], pz = A.z[cur][iq];
+  double nx = px, ny = py, nzp = pz;
+  uint8_t nfl = 0;
+  bool write_pos = (fl & FL_MOVED) != 0;
+  if (is_static) {
+    nfl = FL_STATIC;
+    c_static++;
+    Fx = Fy = Fz = 0.0;
+  } else {
+    const uint8_t beh = A.beh[iq];
+    if (PREC == 1) {
+      float ux = 0.f, uy = 0.f, uz = 0.f;
+      const float fn2 = fmaf(ffx, ffx, fmaf(ffy, ffy, ffz * ffz));
+      if (fn2 > P.adherencef * P.adherencef) {
+        ux = dt_f * ffx; uy = dt_f * ffy; uz = dt_f * ffz;
+        const float dn2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+        if (dn2 > P.dmaxf * P.dmaxf) {
+          const float c = P.dmaxf * rsqrtf(dn2);
+          ux *= c; uy *= c; uz *= c;
+        }
+      }
+      if (P.walk && (beh & BEH_WALK)) {
+        float u[3];
+        unit_vector_f32(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
+        ux = fmaf(P.walkf, u[0], ux);
+        uy = fmaf(P.walkf, u[1], uy);
+        uz = fmaf(P.walkf, u[2], uz);
+      }
+      if (ux != 0.f) nx = __dadd_rn(px, ftod_exact(ux));
+      if (uy != 0.f) ny = __dadd_rn(py, ftod_exact(uy));
+      if (uz != 0.f) nzp = __dadd_rn(pz, ftod_exact(uz));
+    } else {
+      double ux = 0.0, uy = 0.0, uz = 0.0;
+      const double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dfx, dfx), __dmul_rn(dfy, dfy)), __dmul_rn(dfz, dfz)));
+      if (fn > P.adherence) {
+        ux = __dmul_rn(dt, dfx); uy = __dmul_rn(dt, dfy); uz = __dmul_rn(dt, dfz);
+        const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
+        if (dn > P.dmax) {
+          const double c = __ddiv_rn(P.dmax, dn);
+          ux = __dmul_rn(ux, c); uy = __dmul_rn(uy, c); uz = __dmul_rn(uz, c);
+        }
+      }
+      if (P.walk && (beh & BEH_WALK)) {
+        double u[3];
+        unit_vector_f64(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
+        ux = __dadd_rn(ux, __dmul_rn(P.walk_step, u[0]));
+        uy = __dadd_rn(uy, __dmul_rn(P.walk_step, u[1]));
+        uz = __dadd_rn(uz, __dmul_rn(P.walk_step, u[2]));
+      }
+      nx = __dadd_rn(px, ux);
+      ny = __dadd_rn(py, uy);
+      nzp = __dadd_rn(pz, uz);
+    }
+    const bool moved = (nx != px) || (ny != py) || (nzp != pz);
+    bool changed = moved;
+    if (PREC == 0 && P.grow && (beh & BEH_GROW)) {
+      const double pi = 3.141592653589793;
+      const double v = __dadd_rn(A.vol[iq], P.growth);
+      changed = true;
+      if (v >= P.divide_volume) {
+        const uint64_t uid = A.uid[iq];
+        const double u0 = uniform_draw(P.seed, uid, (uint64_t)step, PURPOSE_RATIO);
+        const double rho = __dadd_rn(P.ratio_lo, __dmul_rn(__dsub_rn(P.ratio_hi, P.ratio_lo), u0));
+        const double v1 = __ddiv_rn(__dmul_rn(v, rho), __dadd_rn(1.0, rho));
+        const double v2 = __ddiv_rn(v, __dadd_rn(1.0, rho));
+        double ax[3];
+        unit_vector_f64(P.seed, uid, (uint64_t)step, PURPOSE_AXIS, ax);
+        const double rad = __dmul_rn(cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi)), 0.5);
+        const double a1 = __dmul_rn(rad, __ddiv_rn(v2, v)), a2 = __dmul_rn(rad, __ddiv_rn(v1, v));
+        const double cx = nx, cy = ny, cz = nzp;
+        nx = __dadd_rn(cx, __dmul_rn(a1, ax[0]));
+        ny = __dadd_rn(cy, __dmul_rn(a1, ax[1]));
+        nzp = __dadd_rn(cz, __dmul_rn(a1, ax[2]));
+        B.stash[iq] = mk_dbl4(__dsub_rn(cx, __dmul_rn(a2, ax[0])), __dsub_rn(cy, __dmul_rn(a2, ax[1])),
+                                   __dsub_rn(cz, __dmul_rn(a2, ax[2])), v2);
+        A.vol[iq] = v1;
+        ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v1), pi));
+        nfl |= FL_DIVIDE | FL_MOVED;
+        write_pos = true;
+      } else {
+        A.vol[iq] = v;
+        ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi));
+      }
+    }
+    if (moved) { nfl |= FL_MOVED; c_moved++; write_pos = true; }
+    if (changed) nfl |= FL_CHANGED;
+    A.nz[iq] = (uint16_t)min(ncont, 65535u);
+  }
+  if (write_pos) {
+    A.x[nxt][iq] = nx;
+    A.y[nxt][iq] = ny;
+    A.z[nxt][iq] = nzp;
+  }
+  A.flags[iq] = nfl;
+  if (P.keep_forces) { B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz; }
+  atomicMin(&bb_w[0], enc_f64(nx));
+  atomicMax(&bb_w[3], enc_f64(nx));
+  atomicMin(&bb_w[1], enc_f64(ny));
+  atomicMax(&bb_w[4], enc_f64(ny));
+  atomicMin(&bb_w[2], enc_f64(nzp));
+  atomicMax(&bb_w[5], enc_f64(nzp));
+}
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevParams P) {
   __shared__ int s_nocc[27];
@@ -574,117 +702,447 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         c_cont += ncont;
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
-        double Fx, Fy, Fz;
-        if (PREC == 0) { Fx = dfx; Fy = dfy; Fz = dfz; }
-        else { Fx = ftod_exact(ffx); Fy = ftod_exact(ffy); Fz = ftod_exact(ffz); }
-        if (MODE == FM_FORCES) {
-          B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz;
-          B.dbg_i32[iq] = (int32_t)ncont;
-          B.dbg_i32[B.cap + iq] = (int32_t)nnb;
-          continue;
-        }
-        // ----------------------------------------------------- FM_STEP epilogue
-        const double px = A.x[cur][iq], py = A.y[cur][iq], pz = A.z[cur][iq];
-        double nx = px, ny = py, nzp = pz;
-        uint8_t nfl = 0;
-        bool write_pos = (fl & FL_MOVED) != 0;
-        if (is_static) {
-          nfl = FL_STATIC;
-          c_static++;
-          Fx = Fy = Fz = 0.0;
+        finish_agent<PREC, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, ffx, ffy, ffz, dfx, dfy, dfz,
+                                 nnb, ncont, c_static, c_moved, s_bb[warp]);
+      }
+    }
+  }
+  if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = wsum64(c_cand),
+                           t_nbr = wsum64(c_nbr), t_cont = wsum64(c_cont), t_exact = wsum64(c_exact);
+  if (lane == 0) {
+    if (t_static) atomicAdd(&C->a_static, t_static);
+    if (t_moved) atomicAdd(&C->a_moved, t_moved);
+    if (t_cand) atomicAdd(&C->a_cand, t_cand);
+    if (t_nbr) atomicAdd(&C->a_nbr, t_nbr);
+    if (t_cont) atomicAdd(&C->a_contact, t_cont);
+    if (t_exact) atomicAdd(&C->a_exact, t_exact);
+  }
+}
+
+// Exact FP64 inputs of a pair, for the out-of-line settle step of k_force32.
+struct ExactSrc {
+  const uint32_t *perm;
+  const double *x, *y, *z;
+  const float4 *c32;
+  double R2, k, gamma;
+};
+
+// Settle the deferred pairs of a k_force32 warp (called by the whole warp).
+// Entry e holds the candidate's sorted index and the agent slot and kind in
+// dw[e], and for a grazing pair its FP32 contribution and error bound in
+// dc[e].  Band pairs are evaluated in FP64 and added with their neighbour and
+// contact counts; the grazing pairs of agents in rmask are redone in FP64,
+// replacing their FP32 contribution and removing their bound.  Each agent's
+// owner lane adds its settled pairs in list order.  kq0 is the sorted index of
+// agent slot 0.  Returns this lane's count of FP64 pair evaluations.
+#define DA_EXACT 0x100u
+#define DA_NBR 0x200u
+#define DA_CONT 0x400u
+__device__ __noinline__ unsigned settle_deferred(ExactSrc X, unsigned kq0, unsigned dlen, unsigned rmask, float4 *dc,
+                                                 uint2 *dw, float4 *acc, float *bnd, uint32_t *nnb_s,
+                                                 uint32_t *nct_s) {
+  const unsigned lane = threadIdx.x & 31;
+  unsigned n_exact = 0;
+  for (unsigned e0 = 0; e0 < dlen; e0 += 32) {
+    const unsigned e = e0 + lane;
+    bool need = false;
+    if (e < dlen) {
+      const uint2 w = dw[e];
+      const unsigned a = w.y & 0xffu;
+      const bool ex = (w.y & DA_EXACT) != 0;
+      need = ex || ((rmask >> a) & 1u);
+      if (need) {
+        n_exact++;
+        const unsigned kq = kq0 + a, kj = w.x;
+        const uint32_t iq = X.perm[kq], ij = X.perm[kj];
+        const dbl4 pq = mk_dbl4(X.x[iq], X.y[iq], X.z[iq], ftod_exact(X.c32[kq].w));
+        const dbl4 pj = mk_dbl4(X.x[ij], X.y[ij], X.z[ij], ftod_exact(X.c32[kj].w));
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        const int r = pair_f64_k(X.R2, X.k, X.gamma, pq, pj, gx, gy, gz);
+        if (ex) {
+          dc[e] = make_float4((float)gx, (float)gy, (float)gz, 0.f);
+          dw[e].y = w.y | (r > 0 ? DA_NBR : 0u) | (r == 2 ? DA_CONT : 0u);
         } else {
-          const uint8_t beh = A.beh[iq];
-          if (PREC == 1) {
-            float ux = 0.f, uy = 0.f, uz = 0.f;
-            const float fn2 = fmaf(ffx, ffx, fmaf(ffy, ffy, ffz * ffz));
-            if (fn2 > P.adherencef * P.adherencef) {
-              ux = dt_f * ffx; uy = dt_f * ffy; uz = dt_f * ffz;
-              const float dn2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-              if (dn2 > P.dmaxf * P.dmaxf) {
-                const float c = P.dmaxf * rsqrtf(dn2);
-                ux *= c; uy *= c; uz *= c;
+          // FP64 contribution in place of the FP32 one; its bound goes
+          const float4 d = dc[e];
+          dc[e] = make_float4((float)gx - d.x, (float)gy - d.y, (float)gz - d.z, d.w);
+        }
+      }
+    }
+    unsigned nm = __ballot_sync(0xffffffffu, need);
+    __syncwarp();
+    for (; nm; nm &= nm - 1) {
+      const unsigned e1 = e0 + (unsigned)(__ffs(nm) - 1);
+      const unsigned w = dw[e1].y;
+      if (lane == (w & 0xffu)) {
+        const float4 d = dc[e1];
+        float4 t = acc[lane];
+        t.x += d.x; t.y += d.y; t.z += d.z;
+        acc[lane] = t;
+        if (w & DA_EXACT) {
+          nnb_s[lane] += (w & DA_NBR) ? 1u : 0u;
+          nct_s[lane] += (w & DA_CONT) ? 1u : 0u;
+        } else {
+          bnd[lane] -= d.w;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  return n_exact;
+}
+
+// ---------------------------------------------------------------- FP32 form: pair-ring kernel
+// The FP32 form's production kernel.  Same work decomposition as k_force
+// (one CTA per occupied brick, one warp per box), but the pairs are not
+// evaluated lane-per-agent.  For a group of up to 32 agents of a box the warp
+// stages the stencil's candidates in shared memory (up to F32_CHUNK at a
+// time; most stencils fit at once); for every agent it tests 32 candidates
+// per instruction in FP32 and appends the (agent, candidate) indices of those
+// inside the cutoff band to a ring (ballot + popcount positions).  Whenever
+// the ring holds 32 pairs they are evaluated with every lane busy, and a
+// segmented shuffle reduction over the agent index folds them into per-agent
+// sums in shared memory.  Pairs that FP32 cannot decide (cutoff or contact
+// band) and grazing contacts are also written to the warp's deferred list in
+// global memory, settled in FP64 at the end of the group: band pairs always,
+// grazing pairs when the agent's summed FP32 error bound is not a small part
+// of its tolerance (their FP32 contribution is then replaced).
+#define F32_WARPS FORCE32_WARPS
+#define F32_MINB FORCE32_CTAS_PER_SM
+#define F32_CHUNK 512
+#define F32_RING 256
+#define F32_DCAP FORCE32_DCAP
+// per warp: staged chunk (float4 + index), the ring, the group's agents and
+// their sums (float4 each), bounds and the two counts (one word each)
+#define F32_WARP_SMEM (F32_CHUNK * 20 + F32_RING * 4 + 32 * 16 * 2 + 32 * 4 * 3)
+
+template <int MODE>
+__global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B, DevParams P) {
+  __shared__ int s_nocc[27];
+  __shared__ unsigned long long s_ndirty[27];
+  __shared__ int s_next;
+  __shared__ long long s_o;
+  __shared__ float4 s_off[27];
+  __shared__ unsigned long long s_bb[F32_WARPS][6];
+  __shared__ unsigned s_pre[F32_WARPS][28], s_st[F32_WARPS][28];
+  extern __shared__ __align__(16) unsigned char dyn_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float4 *const sc = (float4 *)(dyn_smem + (size_t)warp * F32_WARP_SMEM);  // staged candidates
+  float4 *const ag = sc + F32_CHUNK;                                       // the group's agents
+  float4 *const acc = ag + 32;                                             // their sums (f, scale)
+  uint32_t *const skj = (uint32_t *)(acc + 32);                            // staged: sorted index
+  uint32_t *const ring = skj + F32_CHUNK;                                  // (agent << 16) | chunk index
+  float *const bnd = (float *)(ring + F32_RING);                           // summed error bounds
+  uint32_t *const nnb_s = (uint32_t *)(bnd + 32);                          // neighbour counts
+  uint32_t *const nct_s = nnb_s + 32;                                      // contact counts
+  const size_t dbase = ((size_t)blockIdx.x * F32_WARPS + warp) * F32_DCAP;
+  float4 *const dc = B.defer_c + dbase;  // deferred: FP32 contribution, bound
+  uint2 *const dw = B.defer_w + dbase;   // deferred: sorted index, agent | kind
+
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet &A = *B.A;  // read at the use sites: no registers held
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
+  const long long n_occ = C->n_occ;
+  const long long step = C->step;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
+  int wsim = -1;
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
+  }
+  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
+
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_o = (long long)atomicAdd((unsigned long long *)&C->work_next, 1ull);
+      s_next = 0;
+    }
+    __syncthreads();
+    const long long o = s_o;
+    if (o >= n_occ) break;
+    const int4 info = B.occ_info[o];
+    const SimGeom &G = B.geom[info.w];
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x;
+      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
+      int occ = -1;
+      unsigned long long dm = 0ull;
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
+        occ = B.brick_occ[rank];
+        if (use_static) dm = B.dirty[rank];
+      }
+      s_nocc[t] = occ;
+      s_ndirty[t] = dm;
+    }
+    __syncthreads();
+    if (MODE == FM_STEP && info.w != wsim) {
+      flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+      wsim = info.w;
+    }
+    const double dt = G.dt;
+    const float dt_f = G.dt_f;
+
+    while (true) {
+      int lb = 0;
+      if (lane == 0) lb = atomicAdd(&s_next, 1);
+      lb = __shfl_sync(0xffffffffu, lb, 0);
+      if (lb >= 64) break;
+      const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
+      if (nq == 0) continue;
+      int lx, ly, lz;
+      local_decode(lb, lx, ly, lz);
+      unsigned nb_st = 0, nb_cnt = 0;
+      bool nb_dirty = false;
+      if (lane < 27) {
+        const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
+        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+        const int lc = local_code(ax & 3, ay & 3, az & 3);
+        const int occ = s_nocc[bo];
+        if (occ >= 0) {
+          nb_st = B.box_start[(long long)occ * 64 + lc];
+          nb_cnt = B.box_cnt[(long long)occ * 64 + lc];
+        }
+        nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
+      }
+      const bool clean = !__any_sync(0xffffffffu, nb_dirty);
+      unsigned pre = nb_cnt;
+      for (int of = 1; of < 32; of <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
+        if (lane >= of) pre += y;
+      }
+      const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
+      if (lane < 27) {
+        s_pre[warp][lane] = pre - nb_cnt;
+        s_st[warp][lane] = nb_st;
+      }
+      __syncwarp();
+
+      for (unsigned q0 = 0; q0 < nq; q0 += 32) {
+        const unsigned ng = min(32u, nq - q0);
+        const bool valid = (unsigned)lane < ng;
+        const unsigned kq = qbase + q0 + (valid ? (unsigned)lane : 0u);
+        const uint32_t iq = B.perm[kq];
+        const float4 cq = B.c32[kq];
+        const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
+        const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+        const bool compute = valid && !is_static;
+        ag[lane] = cq;
+        acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        bnd[lane] = 0.f;
+        nnb_s[lane] = 0u;
+        nct_s[lane] = 0u;
+        const unsigned cmask = __ballot_sync(0xffffffffu, compute);
+        __syncwarp();
+        if (cmask) {
+          unsigned dlen = 0;
+          // evaluate cnt (<= 32) ring pairs starting at ring position h
+          auto drain = [&](unsigned h, unsigned cnt) {
+            const bool v = (unsigned)lane < cnt;
+            const unsigned ent = v ? ring[(h & (F32_RING - 1)) + (unsigned)lane] : 0u;
+            const unsigned a = ent >> 16, i = ent & 0xffffu;
+            const float4 q = ag[a];
+            const float4 c = sc[i];
+            const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+            const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+            const float s = q.w + c.w, s2 = s * s;
+            const float W = fmaf(s, P.cband1, s2 * P.cband2);
+            const bool exact = v && (band || (d2 > s2 - W && d2 < s2 + W));
+            const bool cont = v && !exact && d2 <= s2 - W;
+            float vx = 0.f, vy = 0.f, vz = 0.f, vs = 0.f, vb = 0.f;
+            bool graze = false;
+            if (cont) {
+              const float inv_d = rsqrtf(d2);
+              const float d = d2 * inv_d;
+              const float delta = s - d;
+              const float rbar = __fdividef(q.w * c.w, s);
+              const float rd = rbar * delta;
+              const float sq = rd * rsqrtf(rd);
+              const float kd = P.kf * delta, gs = P.gammaf * sq;
+              const float scf = (kd - gs) * inv_d;
+              vx = scf * ex;
+              vy = scf * ey;
+              vz = scf * ez;
+              vs = kd + gs;
+              graze = delta < P.graze;
+              if (graze) {
+                // d/d(delta) of sqrt(rbar delta) is large: bound its FP32 error
+                vb = (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
+                                           P.gammaf * sqrtf(rbar * P.graze_e))
+                                   : P.gammaf * sqrtf(rbar * P.graze_e);
               }
             }
-            if (P.walk && (beh & BEH_WALK)) {
-              float u[3];
-              unit_vector_f32(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
-              ux = fmaf(P.walkf, u[0], ux);
-              uy = fmaf(P.walkf, u[1], uy);
-              uz = fmaf(P.walkf, u[2], uz);
+            const bool defer = exact || graze;
+            const unsigned dbal = __ballot_sync(0xffffffffu, defer);
+            if (dbal) {
+              if (dlen + (unsigned)__popc(dbal) > F32_DCAP) {
+                // full list: settle it now, redoing every grazing pair in it
+                c_exact += settle_deferred(ExactSrc{B.perm, A.x[cur], A.y[cur], A.z[cur], B.c32, P.R2, P.k, P.gamma},
+                                           qbase + q0, dlen, 0xffffffffu, dc, dw, acc, bnd, nnb_s, nct_s);
+                dlen = 0;
+              }
+              if (defer) {
+                const unsigned p = dlen + (unsigned)__popc(dbal & lt_mask);
+                dc[p] = make_float4(vx, vy, vz, vb);
+                dw[p] = make_uint2(skj[i], a | (exact ? DA_EXACT : 0u));
+              }
+              dlen += (unsigned)__popc(dbal);
             }
-            if (ux != 0.f) nx = __dadd_rn(px, ftod_exact(ux));
-            if (uy != 0.f) ny = __dadd_rn(py, ftod_exact(uy));
-            if (uz != 0.f) nzp = __dadd_rn(pz, ftod_exact(uz));
-          } else {
-            double ux = 0.0, uy = 0.0, uz = 0.0;
-            const double fn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dfx, dfx), __dmul_rn(dfy, dfy)), __dmul_rn(dfz, dfz)));
-            if (fn > P.adherence) {
-              ux = __dmul_rn(dt, dfx); uy = __dmul_rn(dt, dfy); uz = __dmul_rn(dt, dfz);
-              const double dn = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(ux, ux), __dmul_rn(uy, uy)), __dmul_rn(uz, uz)));
-              if (dn > P.dmax) {
-                const double c = __ddiv_rn(P.dmax, dn);
-                ux = __dmul_rn(ux, c); uy = __dmul_rn(uy, c); uz = __dmul_rn(uz, c);
+            const unsigned nbal = __ballot_sync(0xffffffffu, v && !exact);
+            const unsigned cbal = __ballot_sync(0xffffffffu, cont);
+            // segmented reduction over runs of equal agent index
+            const unsigned key = v ? a : 32u + (unsigned)lane;
+            const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
+            const bool is_head = lane == 0 || prev != key;
+            const unsigned heads = __ballot_sync(0xffffffffu, is_head);
+            const unsigned above = heads & ~(0xffffffffu >> (31 - lane));
+            const unsigned end = above ? (unsigned)(__ffs(above) - 1) : 32u;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const float tx = __shfl_down_sync(0xffffffffu, vx, off);
+              const float ty = __shfl_down_sync(0xffffffffu, vy, off);
+              const float tz = __shfl_down_sync(0xffffffffu, vz, off);
+              const float ts = __shfl_down_sync(0xffffffffu, vs, off);
+              const float tb = __shfl_down_sync(0xffffffffu, vb, off);
+              if ((unsigned)lane + off < end) { vx += tx; vy += ty; vz += tz; vs += ts; vb += tb; }
+            }
+            const unsigned segm = (end == 32u ? 0xffffffffu : ((1u << end) - 1u)) & ~lt_mask;
+            // a run whose agent is not above the previous run's starts a new
+            // epoch; within an epoch the runs' agents are distinct
+            const unsigned desc = __ballot_sync(0xffffffffu, is_head && lane > 0 && key < prev);
+            const unsigned ep = (unsigned)__popc(desc & (lt_mask | (1u << lane)));
+            const unsigned nep = (unsigned)__popc(desc);
+            for (unsigned e = 0; e <= nep; ++e) {
+              if (is_head && v && ep == e) {
+                float4 t = acc[a];
+                t.x += vx; t.y += vy; t.z += vz; t.w += vs;
+                acc[a] = t;
+                bnd[a] += vb;
+                nnb_s[a] += (unsigned)__popc(nbal & segm);
+                nct_s[a] += (unsigned)__popc(cbal & segm);
+              }
+              __syncwarp();
+            }
+          };
+
+          // Producer/consumer loop: scan (agent, 32-candidate block) steps
+          // until the ring holds 32 pairs, then evaluate one ring window.  A
+          // chunk is restaged only once the ring is empty (its entries index
+          // the staged chunk).
+          unsigned head = 0, tail = 0;
+          const unsigned own0 = s_pre[warp][13] + q0;  // stencil position of agent q0 itself
+          unsigned cnext = 0, cstart = 0, fill = 0, nblk = 0, am = 0, a = 0, b = 0, own = 0;
+          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
+          while (true) {
+            while (tail - head < 32u) {
+              if (am == 0) {
+                if (cnext >= ctot || tail != head) break;
+                // stage the next chunk (coalesced copies, box offset applied)
+                cstart = cnext;
+                fill = min((unsigned)F32_CHUNK, ctot - cstart);
+                cnext += fill;
+                __syncwarp();
+                for (unsigned g0 = 0; g0 < fill; g0 += 128u) {
+                  unsigned kjs[4];
+                  int boxs[4];
+#pragma unroll
+                  for (int m = 0; m < 4; ++m) {
+                    const unsigned p = cstart + g0 + lane + 32u * m;
+                    int lo = 0;
+#pragma unroll
+                    for (int st = 16; st > 0; st >>= 1)
+                      if (lo + st <= 26 && s_pre[warp][lo + st] <= p) lo += st;
+                    boxs[m] = lo;
+                    kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
+                  }
+                  float4 cs[4];
+#pragma unroll
+                  for (int m = 0; m < 4; ++m)
+                    if (g0 + lane + 32u * m < fill) cs[m] = __ldg(&B.c32[kjs[m]]);
+#pragma unroll
+                  for (int m = 0; m < 4; ++m) {
+                    const unsigned t = g0 + lane + 32u * m;
+                    if (t < fill) {
+                      const float4 of = s_off[boxs[m]];
+                      sc[t] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
+                      skj[t] = kjs[m];
+                    }
+                  }
+                }
+                __syncwarp();
+                if (lane == 0) c_cand += (unsigned)__popc(cmask) * fill;
+                nblk = (fill + 31u) >> 5;
+                am = cmask;
+                b = 0;
+                a = (unsigned)(__ffs(am) - 1);
+                q = ag[a];
+                own = own0 + a - cstart;
+              }
+              // four candidate blocks of agent a per step (independent chains)
+              unsigned bal[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const unsigned i = (b + u) * 32u + (unsigned)lane;
+                const float4 c = sc[min(i, (unsigned)F32_CHUNK - 1u)];
+                const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                bal[u] = __ballot_sync(0xffffffffu, i < fill && d2 < P.R2_hi_f && i != own);
+              }
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                if ((bal[u] >> lane) & 1u)
+                  ring[(tail + (unsigned)__popc(bal[u] & lt_mask)) & (F32_RING - 1)] = (a << 16) | ((b + u) * 32u + lane);
+                tail += (unsigned)__popc(bal[u]);
+              }
+              b += 4;
+              if (b >= nblk) {
+                b = 0;
+                am &= am - 1;
+                if (am) {
+                  a = (unsigned)(__ffs(am) - 1);
+                  q = ag[a];
+                  own = own0 + a - cstart;
+                }
               }
             }
-            if (P.walk && (beh & BEH_WALK)) {
-              double u[3];
-              unit_vector_f64(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
-              ux = __dadd_rn(ux, __dmul_rn(P.walk_step, u[0]));
-              uy = __dadd_rn(uy, __dmul_rn(P.walk_step, u[1]));
-              uz = __dadd_rn(uz, __dmul_rn(P.walk_step, u[2]));
+            // the producer stops short of 32 pairs only to restage or finish
+            const bool flush = tail - head < 32u;
+            const unsigned cnt = min(32u, tail - head);
+            if (cnt) {
+              __syncwarp();
+              drain(head, cnt);
             }
-            nx = __dadd_rn(px, ux);
-            ny = __dadd_rn(py, uy);
-            nzp = __dadd_rn(pz, uz);
-          }
-          const bool moved = (nx != px) || (ny != py) || (nzp != pz);
-          bool changed = moved;
-          if (PREC == 0 && P.grow && (beh & BEH_GROW)) {
-            const double pi = 3.141592653589793;
-            const double v = __dadd_rn(A.vol[iq], P.growth);
-            changed = true;
-            if (v >= P.divide_volume) {
-              const uint64_t uid = A.uid[iq];
-              const double u0 = uniform_draw(P.seed, uid, (uint64_t)step, PURPOSE_RATIO);
-              const double rho = __dadd_rn(P.ratio_lo, __dmul_rn(__dsub_rn(P.ratio_hi, P.ratio_lo), u0));
-              const double v1 = __ddiv_rn(__dmul_rn(v, rho), __dadd_rn(1.0, rho));
-              const double v2 = __ddiv_rn(v, __dadd_rn(1.0, rho));
-              double ax[3];
-              unit_vector_f64(P.seed, uid, (uint64_t)step, PURPOSE_AXIS, ax);
-              const double rad = __dmul_rn(cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi)), 0.5);
-              const double a1 = __dmul_rn(rad, __ddiv_rn(v2, v)), a2 = __dmul_rn(rad, __ddiv_rn(v1, v));
-              const double cx = nx, cy = ny, cz = nzp;
-              nx = __dadd_rn(cx, __dmul_rn(a1, ax[0]));
-              ny = __dadd_rn(cy, __dmul_rn(a1, ax[1]));
-              nzp = __dadd_rn(cz, __dmul_rn(a1, ax[2]));
-              B.stash[iq] = mk_dbl4(__dsub_rn(cx, __dmul_rn(a2, ax[0])), __dsub_rn(cy, __dmul_rn(a2, ax[1])),
-                                         __dsub_rn(cz, __dmul_rn(a2, ax[2])), v2);
-              A.vol[iq] = v1;
-              ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v1), pi));
-              nfl |= FL_DIVIDE | FL_MOVED;
-              write_pos = true;
+            if (flush) {
+              head = tail = 0;  // the ring is empty now
+              if (am == 0 && cnext >= ctot) break;
             } else {
-              A.vol[iq] = v;
-              ((double *)A.diam)[iq] = cbrt_newton(__ddiv_rn(__dmul_rn(6.0, v), pi));
+              head += 32u;
             }
           }
-          if (moved) { nfl |= FL_MOVED; c_moved++; write_pos = true; }
-          if (changed) nfl |= FL_CHANGED;
-          A.nz[iq] = (uint16_t)min(ncont, 65535u);
+          if (dlen) {
+            // end of the group: refine the agents whose bound is too large
+            const float4 t = acc[lane];
+            const unsigned rmask = __ballot_sync(0xffffffffu, bnd[lane] > 0.25f * (P.rel_tol * t.w + P.abs_tol));
+            c_exact += settle_deferred(ExactSrc{B.perm, A.x[cur], A.y[cur], A.z[cur], B.c32, P.R2, P.k, P.gamma},
+                                       qbase + q0, dlen, rmask, dc, dw, acc, bnd, nnb_s, nct_s);
+          }
         }
-        if (write_pos) {
-          A.x[nxt][iq] = nx;
-          A.y[nxt][iq] = ny;
-          A.z[nxt][iq] = nzp;
+        if (valid) {
+          const float4 t = acc[lane];
+          const unsigned nnb = nnb_s[lane], ncont = nct_s[lane];
+          c_nbr += nnb;
+          c_cont += ncont;
+          finish_agent<1, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, t.x, t.y, t.z, 0.0, 0.0, 0.0,
+                                nnb, ncont, c_static, c_moved, s_bb[warp]);
         }
-        A.flags[iq] = nfl;
-        if (P.keep_forces) { B.fdbg[iq] = Fx; B.fdbg[B.cap + iq] = Fy; B.fdbg[2 * B.cap + iq] = Fz; }
-        atomicMin(&s_bb[warp][0], enc_f64(nx));
-        atomicMax(&s_bb[warp][3], enc_f64(nx));
-        atomicMin(&s_bb[warp][1], enc_f64(ny));
-        atomicMax(&s_bb[warp][4], enc_f64(ny));
-        atomicMin(&s_bb[warp][2], enc_f64(nzp));
-        atomicMax(&s_bb[warp][5], enc_f64(nzp));
       }
     }
   }
@@ -854,6 +1312,18 @@ __global__ void k_nbr_offsets(DevBufs B) {
 
 void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
   k_reset_work<<<1, 1, 0, s>>>(B);
+  if (P.precision == 1 && P.lanes_fixed == 0 && (mode == FM_STEP || mode == FM_FORCES)) {
+    // the FP32 form's pair-ring kernel (dynamic shared memory above 48 KB)
+    constexpr int smem = F32_WARPS * F32_WARP_SMEM;
+    if (mode == FM_STEP) {
+      cudaFuncSetAttribute(k_force32<FM_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      k_force32<FM_STEP><<<c.force32_blocks, F32_WARPS * 32, smem, s>>>(B, P);
+    } else {
+      cudaFuncSetAttribute(k_force32<FM_FORCES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      k_force32<FM_FORCES><<<c.force32_blocks, F32_WARPS * 32, smem, s>>>(B, P);
+    }
+    return;
+  }
   const int g = c.force_blocks;
 #define LF(PR, MO) k_force<PR, MO><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
   if (P.precision == 0) {
