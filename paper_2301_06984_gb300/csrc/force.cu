@@ -812,7 +812,7 @@ __device__ __noinline__ unsigned settle_deferred(ExactSrc X, unsigned kq0, unsig
 #define F32_WARPS FORCE32_WARPS
 #define F32_MINB FORCE32_CTAS_PER_SM
 #define F32_CHUNK 512
-#define F32_RING 256
+#define F32_RING 512
 #define F32_DCAP FORCE32_DCAP
 // per warp: staged chunk (float4 + index), the ring, the group's agents and
 // their sums (float4 each), bounds and the two counts (one word each)
@@ -1086,10 +1086,10 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
                 q = ag[a];
                 own = own0 + a - cstart;
               }
-              // four candidate blocks of agent a per step (independent chains)
-              unsigned bal[4];
+              // eight candidate blocks of agent a per step (independent chains)
+              unsigned bal[8];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int u = 0; u < 8; ++u) {
                 const unsigned i = (b + u) * 32u + (unsigned)lane;
                 const float4 c = sc[min(i, (unsigned)F32_CHUNK - 1u)];
                 const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
@@ -1097,12 +1097,12 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
                 bal[u] = __ballot_sync(0xffffffffu, i < fill && d2 < P.R2_hi_f && i != own);
               }
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int u = 0; u < 8; ++u) {
                 if ((bal[u] >> lane) & 1u)
                   ring[(tail + (unsigned)__popc(bal[u] & lt_mask)) & (F32_RING - 1)] = (a << 16) | ((b + u) * 32u + lane);
                 tail += (unsigned)__popc(bal[u]);
               }
-              b += 4;
+              b += 8;
               if (b >= nblk) {
                 b = 0;
                 am &= am - 1;
