@@ -87,6 +87,7 @@ SIGNATURES = {
                                      C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]),
     "bdm_noalloc_last_error": (C.c_char_p, []),
     "bdm_autotune": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(Tuning)]),
+    "bdm_set_force_kernel": (C.c_int, [C.c_void_p, C.c_int]),
 }
 
 
@@ -293,6 +294,11 @@ class Simulation:
         t = Tuning()
         self._check(lib().bdm_autotune(self._h, int(trial_steps), int(what), C.byref(t)))
         return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
+
+    def set_force_kernel(self, lanes=0):
+        """FP32 form: 0 = pair-ring kernel, else lanes per agent of the
+        lane-per-agent kernel (1, 2, 4, 8, 16 or 32)."""
+        self._check(lib().bdm_set_force_kernel(self._h, int(lanes)))
 
     # ------------------------------------------------------------------ profiling
     def profile_begin(self):

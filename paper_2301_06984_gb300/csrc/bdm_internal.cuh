@@ -110,7 +110,8 @@ struct DevParams {
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk;
-  int32_t lanes_fixed;              // 0: lanes per agent from the per-box cost model
+  int32_t lanes_fixed;              // FP32 form: 0 = pair-ring kernel (k_force32), else
+                                    // lanes per agent of the lane-per-agent kernel (k_force)
 };
 
 // Everything a kernel reaches, passed by value.

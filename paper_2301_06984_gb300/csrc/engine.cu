@@ -778,6 +778,13 @@ static int apply_params(bdm_sim *s, const bdm_params &P, int lanes) {
   return BDM_OK;
 }
 
+int bdm_set_force_kernel(bdm_sim *s, int lanes) {
+  if (!s) return BDM_EINVAL;
+  if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+    return fail(s, BDM_EINVAL, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
+  return apply_params(s, s->P, lanes);
+}
+
 int bdm_autotune(bdm_sim *s, int trial_steps, int what, bdm_tuning *out) {
   if (!s || trial_steps < 1) return s ? fail(s, BDM_EINVAL, "trial_steps must be >= 1") : BDM_EINVAL;
   if (!s->have_agents) return fail(s, BDM_ESTATE, "bdm_set_agents must come first");

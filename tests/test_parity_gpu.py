@@ -360,6 +360,27 @@ def test_autotune_fp64_keeps_state_and_stays_bit_exact():
     assert np.array_equal(pos, o.positions())
 
 
+@pytest.mark.parametrize("lanes", [0, 1, 2, 4, 32])
+def test_fp32_force_kernels_agree_with_oracle(lanes):
+    # the pair-ring kernel (0) and the lane-per-agent kernel: same exact
+    # neighbour and contact decisions, forces within the FP32 tolerance, on a
+    # workload with crowded boxes (more than 32 agents) and several chunks
+    w = H.small_blobs(n=60_000, seed=17)
+    s = H.gpu_sim(w)
+    s.set_force_kernel(lanes)
+    s.step(2)
+    f_g, nz_g, nnb_g = s.forces_now()
+    a = s.get_agents()
+    o = O.State(a["x"], a["y"], a["z"], a["diam"])
+    f_o, nz_o, nnb_o, scale = o.forces_of(H.oracle_params(w), with_scale=True)
+    assert np.array_equal(nnb_g, nnb_o) and np.array_equal(nz_g, nz_o)
+    H.assert_fp32_forces(f_g, f_o, scale)
+    # the workload exercises boxes of more than one 32-agent group
+    bx = s.grid_boxes()
+    _, occ = np.unique(bx, axis=1, return_counts=True)
+    assert occ.max() > 32
+
+
 def test_autotune_fp32_lanes_keep_tolerance():
     w = H.small_blobs(n=40_000, seed=13)
     s = H.gpu_sim(w)
