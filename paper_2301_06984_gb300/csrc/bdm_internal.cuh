@@ -88,6 +88,10 @@ struct DevCounters {
   long long need_bricks, need_occ;
   int32_t sort_now, force_sort;
   unsigned long long work_next;  // dynamic brick fetch of the force kernel
+  // the force kernels take the heaviest bricks first: bricks of at least
+  // FORCE_HEAVY_HI agents (heavy list front), then of at least FORCE_HEAVY_LO
+  // (heavy list back), then the rest in Morton order
+  unsigned long long heavy_n[2], heavy_take[2];
   // per-iteration accumulators (reset by the geometry kernel)
   unsigned long long a_static, a_moved, a_cand, a_nbr, a_contact, a_exact;
   // snapshot of the last completed iteration
@@ -141,6 +145,7 @@ struct DevBufs {
   long long *nbr_off;
   long long *nbr_out;
   int32_t *dbg_i32;               // debug: contacts / neighbours
+  int32_t *heavy;                 // occ_cap: occupied indices of heavy bricks (both ends)
   float4 *defer_c;                // FP32-form deferred pairs: contribution, bound
   uint2 *defer_w;                 // FP32-form deferred pairs: index, agent | kind
   long long brick_cap, occ_cap, cap, nbr_cap;
@@ -241,6 +246,10 @@ struct LaunchCfg {
   int force_blocks;    // k_force (FP64 form, neighbour modes, fixed lanes per agent)
   int force32_blocks;  // k_force32 (FP32 form)
 };
+
+// brick weight classes of the force kernels' largest-first order (agents)
+#define FORCE_HEAVY_HI 1024
+#define FORCE_HEAVY_LO 256
 
 // the FP32 form's pair-ring force kernel: resident CTAs per SM, warps per
 // CTA, and capacity of each warp's deferred-pair list (global memory)

@@ -204,6 +204,7 @@ static int alloc_grid(bdm_sim *s, long long brick_cap, long long occ_cap) {
   A((void **)&B.dirty, sizeof(unsigned long long) * brick_cap);
   A((void **)&B.occ_list, sizeof(int32_t) * occ_cap);
   A((void **)&B.occ_info, sizeof(int4) * occ_cap);
+  A((void **)&B.heavy, sizeof(int32_t) * occ_cap);
   A((void **)&B.box_start, sizeof(uint32_t) * occ_cap * 64);
   A((void **)&B.box_cnt, sizeof(uint32_t) * occ_cap * 64);
   A((void **)&B.scan_a, sizeof(uint32_t) * scan_n);

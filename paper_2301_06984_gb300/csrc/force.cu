@@ -222,6 +222,24 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 #define FORCE_WARPS 8
 #define CHUNK 96
 
+// Next occupied brick for a force-kernel CTA (called by one thread; phase is
+// that thread's cursor, starting at 0): the heaviest bricks first, so that no
+// CTA starts a dense brick when the others are about to run out of work.
+// Returns -1 when every brick has been handed out.
+__device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCounters *C, long long n_occ, int &phase) {
+  while (true) {
+    if (phase < 2) {
+      const unsigned long long u = atomicAdd(&C->heavy_take[phase], 1ull);
+      if (u < C->heavy_n[phase]) return phase == 0 ? B.heavy[u] : B.heavy[B.occ_cap - 1 - (long long)u];
+      phase++;
+      continue;
+    }
+    const long long o = (long long)atomicAdd(&C->work_next, 1ull);
+    if (o >= n_occ) return -1;
+    if (B.brick_count[B.occ_list[o]] < FORCE_HEAVY_LO) return o;  // heavy ones were listed
+  }
+}
+
 // flush a warp's shared bounding-box accumulator into the simulation's
 __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParams &P, int nxt, int sim,
                                                 unsigned long long *bb_w) {
@@ -384,6 +402,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   const long long step = C->step;
   unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
   int wsim = -1;
+  int fetch_phase = 0;
   if (threadIdx.x < 27) {
     const int t = threadIdx.x;
     s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
@@ -395,12 +414,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = (long long)atomicAdd((unsigned long long *)&C->work_next, 1ull);
+      s_o = next_force_brick(B, C, n_occ, fetch_phase);
       s_next = 0;
     }
     __syncthreads();
     const long long o = s_o;
-    if (o >= n_occ) break;
+    if (o < 0) break;
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
     if (threadIdx.x < 27) {
@@ -851,6 +870,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   const unsigned lt_mask = (1u << lane) - 1u;
   unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
   int wsim = -1;
+  int fetch_phase = 0;
   if (threadIdx.x < 27) {
     const int t = threadIdx.x;
     s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
@@ -860,12 +880,12 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = (long long)atomicAdd((unsigned long long *)&C->work_next, 1ull);
+      s_o = next_force_brick(B, C, n_occ, fetch_phase);
       s_next = 0;
     }
     __syncthreads();
     const long long o = s_o;
-    if (o >= n_occ) break;
+    if (o < 0) break;
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
     if (threadIdx.x < 27) {
@@ -1159,7 +1179,10 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   }
 }
 
-__global__ void k_reset_work(DevBufs B) { B.ctr->work_next = 0; }
+__global__ void k_reset_work(DevBufs B) {
+  B.ctr->work_next = 0;
+  B.ctr->heavy_take[0] = B.ctr->heavy_take[1] = 0;
+}
 
 // ---------------------------------------------------------------- division merge
 // Daughter slot = n + (number of dividing agents with a smaller storage

@@ -200,6 +200,7 @@ __global__ void k_geometry(DevBufs B, DevParams P) {
     C->n_div = 0;
     C->max_brick = 0;
     C->n_occ = 0;
+    C->heavy_n[0] = C->heavy_n[1] = 0;
     C->sort_now = ((P.sort_every > 0 && (C->step % P.sort_every) == 0) || C->force_sort) ? 1 : 0;
     C->force_sort = 0;
   }
@@ -440,6 +441,11 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
     const unsigned S0 = B.brick_start[g];
     const unsigned m = B.brick_count[g];
     const bool onchip = m <= BS_SMEM_M;
+    if (threadIdx.x == 0 && m >= FORCE_HEAVY_LO) {
+      // heavy bricks, listed for the force kernels' largest-first order
+      if (m >= FORCE_HEAVY_HI) B.heavy[atomicAdd(&C->heavy_n[0], 1ull)] = (int32_t)o;
+      else B.heavy[B.occ_cap - 1 - (long long)atomicAdd(&C->heavy_n[1], 1ull)] = (int32_t)o;
+    }
     __syncthreads();
     if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
     if (threadIdx.x == 0) s_abort = 0;

@@ -47,7 +47,8 @@ constexpr size_t OFF_BOCC = align_up(OFF_BSTART + NA_MAX_BRICKS * 4);
 constexpr size_t OFF_DIRTY = align_up(OFF_BOCC + NA_MAX_BRICKS * 4);
 constexpr size_t OFF_OCCL = align_up(OFF_DIRTY + NA_MAX_BRICKS * 8);
 constexpr size_t OFF_OCCI = align_up(OFF_OCCL + NA_MAX_OCC * 4);
-constexpr size_t OFF_BOXS = align_up(OFF_OCCI + NA_MAX_OCC * sizeof(int4));
+constexpr size_t OFF_HEAVY = align_up(OFF_OCCI + NA_MAX_OCC * sizeof(int4));
+constexpr size_t OFF_BOXS = align_up(OFF_HEAVY + NA_MAX_OCC * 4);
 constexpr size_t OFF_BOXC = align_up(OFF_BOXS + NA_MAX_OCC * 64 * 4);
 constexpr size_t SCAN_N = (NA_MAX_BRICKS + SCAN_TILE - 1) / SCAN_TILE + 2;
 constexpr size_t OFF_SCANA = align_up(OFF_BOXC + NA_MAX_OCC * 64 * 4);
@@ -135,6 +136,7 @@ extern "C" int bdm_forces_noalloc(int64_t n, const double *xyz, const double *di
   B.dirty = (unsigned long long *)(base + OFF_DIRTY);
   B.occ_list = (int32_t *)(base + OFF_OCCL);
   B.occ_info = (int4 *)(base + OFF_OCCI);
+  B.heavy = (int32_t *)(base + OFF_HEAVY);
   B.box_start = (uint32_t *)(base + OFF_BOXS);
   B.box_cnt = (uint32_t *)(base + OFF_BOXC);
   B.key = (uint32_t *)(base + OFF_KEY);
