@@ -53,6 +53,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="blobs", choices=["blobs", "ensemble", "core_shell", "lattice", "uniform"],
                     help="blobs is the headline; the others measure the remaining configurations")
+    ap.add_argument("--sort-every", type=int, default=10,
+                    help="blobs: Morton re-sort cadence (0 = never; the headline workload uses 10)")
+    ap.add_argument("--presort", action="store_true",
+                    help="blobs: put storage in Morton order (bdm_sort) before the warm-up")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble: skip the autotuner")
     return ap.parse_args()
 
 
@@ -72,6 +77,8 @@ def config(args):
         "n_agents": args.n,
         "precision": "FP32 pair force and accumulation; FP64 cutoff predicate, contact decision and positions",
         "l2_policy": "inputs larger than L2 (about 1 GB touched per iteration vs 129 MB L2); no flush",
+        "sort_every": args.sort_every,
+        "presort": bool(args.presort),
         "parallelism": "replica per GPU" if args.gpus > 1 else "single GPU",
     }
 
@@ -238,13 +245,17 @@ def run_other(args):
         w = W.ensemble()
         sim = bdm.Simulation.from_workload(w)
         sim.set_workload(w)
+        tuning = None
+        if not args.no_autotune:
+            # box edge, force kernel (threads per box pair) and sort cadence
+            tuning = sim.autotune(trial_steps=3)
         sim.step(args.warmup)
         ms = timed_steps(sim, args.steps, stream)
         line.update(value=w.n * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps, dtype="f32",
                     config={"workload": "ensemble-512: 512 independent simulations, 10^U[3,5] agents each, "
                                         "0.25 volume fraction cubes, d = 10 um, dt U[0.005,0.02]; all "
                                         "simulations in one CUDA-graph launch sequence per iteration",
-                            "n_agents": w.n, "n_sims": w.n_sims})
+                            "n_agents": w.n, "n_sims": w.n_sims, "autotuned": tuning})
         # baseline: one simulation object (own graph) per member, launched one after another
         sims = []
         for m in range(w.n_sims):
@@ -335,8 +346,10 @@ def main():
 
     w = workload(args.n)
     stream = torch.cuda.current_stream()
-    sim = bdm.Simulation.from_workload(w, precision="fp32", sort_every=10)
+    sim = bdm.Simulation.from_workload(w, precision="fp32", sort_every=args.sort_every)
     sim.set_workload(w)
+    if args.presort:
+        sim.sort()
     sim.step(max(3, args.warmup))
     torch.cuda.synchronize()
 

@@ -240,6 +240,41 @@ __device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCount
   }
 }
 
+// Static-brick pass (FM_STEP with static detection; called by the whole CTA
+// once s_ndirty holds the masks of the brick and its 26 neighbours).  When no
+// box there is dirty, an agent of the brick is static exactly when it did not
+// change in the previous iteration and had at most one contact; if all of
+// them are, the CTA finishes the brick as one streaming pass over its agents
+// (flag, bounding box, zero force), with the result the per-box path gives a
+// static agent, and returns true.  Otherwise it returns false.
+__device__ bool static_brick_pass(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, long long o,
+                                  const unsigned long long *s_ndirty, unsigned &c_static,
+                                  unsigned long long *bb_w) {
+  const int clean = (threadIdx.x < 27) ? (s_ndirty[threadIdx.x] == 0ull) : 1;
+  if (!__syncthreads_and(clean)) return false;
+  const int g = B.occ_list[o];
+  const unsigned S0 = B.brick_start[g], m = B.brick_count[g];
+  int all = 1;
+  for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+    const uint32_t iq = B.perm[S0 + k];
+    all &= !(A.flags[iq] & FL_CHANGED) && A.nz[iq] <= 1;
+  }
+  if (!__syncthreads_and(all)) return false;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+    const uint32_t iq = B.perm[S0 + k];
+    if (A.flags[iq] != FL_STATIC) A.flags[iq] = FL_STATIC;
+    const unsigned long long e[3] = {enc_f64(A.x[cur][iq]), enc_f64(A.y[cur][iq]), enc_f64(A.z[cur][iq])};
+    for (int d = 0; d < 3; ++d) { mn[d] = min(mn[d], e[d]); mx[d] = max(mx[d], e[d]); }
+    if (P.keep_forces) { B.fdbg[iq] = 0.0; B.fdbg[B.cap + iq] = 0.0; B.fdbg[2 * B.cap + iq] = 0.0; }
+    c_static++;
+  }
+  for (int d = 0; d < 3; ++d) { mn[d] = wmin64(mn[d]); mx[d] = wmax64(mx[d]); }
+  if ((threadIdx.x & 31) == 0 && mn[0] != ~0ull)
+    for (int d = 0; d < 3; ++d) { atomicMin(&bb_w[d], mn[d]); atomicMax(&bb_w[3 + d], mx[d]); }
+  return true;
+}
+
 // flush a warp's shared bounding-box accumulator into the simulation's
 __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParams &P, int nxt, int sim,
                                                 unsigned long long *bb_w) {
@@ -253,8 +288,9 @@ __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParam
   __syncwarp();
 }
 
-// Per-agent end of the force kernels.  FM_FORCES records the summed force
-// and the contact and neighbour counts in the debug buffers.  FM_STEP forms
+// Per-agent end of the force kernels (px, py, pz: the agent's position P_t).
+// FM_FORCES records the summed force and the contact and neighbour counts in
+// the debug buffers.  FM_STEP forms
 // the displacement (Sec. 5: dt F unless |F| <= adherence, clamped to the
 // maximum displacement, random walk added after the clamp), grows and divides
 // (FP64 form), writes the new position when it or the previous one moved,
@@ -264,7 +300,8 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
                                              long long step, double dt, float dt_f, uint32_t iq, uint8_t fl,
                                              bool is_static, float ffx, float ffy, float ffz, double dfx, double dfy,
                                              double dfz, unsigned nnb, unsigned ncont, unsigned &c_static,
-                                             unsigned &c_moved, unsigned long long *bb_w) {
+                                             unsigned &c_moved, unsigned long long *bb_w, double px, double py,
+                                             double pz) {
   double Fx, Fy, Fz;
   if (PREC == 0) { Fx = dfx; Fy = dfy; Fz = dfz; }
   else { Fx = ftod_exact(ffx); Fy = ftod_exact(ffy); Fz = ftod_exact(ffz); }
@@ -275,7 +312,6 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
     return;
   }
   // ----------------------------------------------------- FM_STEP epilogue
-  const double px = A.x[cur][iq], py = A.y[cur][iq], pz = A.z[cur][iq];
   double nx = px, ny = py, nzp = pz;
   uint8_t nfl = 0;
   bool write_pos = (fl & FL_MOVED) != 0;
@@ -284,7 +320,7 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
     c_static++;
     Fx = Fy = Fz = 0.0;
   } else {
-    const uint8_t beh = A.beh[iq];
+    const uint8_t beh = (P.walk || P.grow) ? A.beh[iq] : (uint8_t)0;
     if (PREC == 1) {
       float ux = 0.f, uy = 0.f, uz = 0.f;
       const float fn2 = fmaf(ffx, ffx, fmaf(ffy, ffy, ffz * ffz));
@@ -440,6 +476,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
+    if (MODE == FM_STEP && use_static && static_brick_pass(B, P, A, cur, o, s_ndirty, c_static, s_bb[warp]))
+      continue;
     const double dt = G.dt;
     const float dt_f = G.dt_f;
 
@@ -721,8 +759,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         c_cont += ncont;
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
+        double px = 0.0, py = 0.0, pz = 0.0;
+        if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
         finish_agent<PREC, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, ffx, ffy, ffz, dfx, dfy, dfz,
-                                 nnb, ncont, c_static, c_moved, s_bb[warp]);
+                                 nnb, ncont, c_static, c_moved, s_bb[warp], px, py, pz);
       }
     }
   }
@@ -830,12 +870,13 @@ __device__ __noinline__ unsigned settle_deferred(ExactSrc X, unsigned kq0, unsig
 // of its tolerance (their FP32 contribution is then replaced).
 #define F32_WARPS FORCE32_WARPS
 #define F32_MINB FORCE32_CTAS_PER_SM
-#define F32_CHUNK 512
+#define F32_CHUNK 448
 #define F32_RING 512
 #define F32_DCAP FORCE32_DCAP
-// per warp: staged chunk (float4 + index), the ring, the group's agents and
-// their sums (float4 each), bounds and the two counts (one word each)
-#define F32_WARP_SMEM (F32_CHUNK * 20 + F32_RING * 4 + 32 * 16 * 2 + 32 * 4 * 3)
+// per warp: staged chunk (float4 + index), the ring, the group's agents,
+// their sums (float4 each) and positions (three doubles), bounds and the two
+// counts (one word each)
+#define F32_WARP_SMEM (F32_CHUNK * 20 + F32_RING * 4 + 32 * 16 * 2 + 32 * 8 * 3 + 32 * 4 * 3)
 
 template <int MODE>
 __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B, DevParams P) {
@@ -851,7 +892,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   float4 *const sc = (float4 *)(dyn_smem + (size_t)warp * F32_WARP_SMEM);  // staged candidates
   float4 *const ag = sc + F32_CHUNK;                                       // the group's agents
   float4 *const acc = ag + 32;                                             // their sums (f, scale)
-  uint32_t *const skj = (uint32_t *)(acc + 32);                            // staged: sorted index
+  double *const pos_s = (double *)(acc + 32);                              // their P_t (x, y, z rows)
+  uint32_t *const skj = (uint32_t *)(pos_s + 96);                          // staged: sorted index
   uint32_t *const ring = skj + F32_CHUNK;                                  // (agent << 16) | chunk index
   float *const bnd = (float *)(ring + F32_RING);                           // summed error bounds
   uint32_t *const nnb_s = (uint32_t *)(bnd + 32);                          // neighbour counts
@@ -906,6 +948,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
+    if (MODE == FM_STEP && use_static && static_brick_pass(B, P, A, cur, o, s_ndirty, c_static, s_bb[warp]))
+      continue;
     const double dt = G.dt;
     const float dt_f = G.dt_f;
 
@@ -959,6 +1003,14 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
         bnd[lane] = 0.f;
         nnb_s[lane] = 0u;
         nct_s[lane] = 0u;
+        if (MODE == FM_STEP && valid) {
+          // the epilogue's P_t, fetched while the pairs are evaluated
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(pos_s + lane);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(A.x[cur] + iq) : "memory");
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa + 256u), "l"(A.y[cur] + iq) : "memory");
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa + 512u), "l"(A.z[cur] + iq) : "memory");
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
         const unsigned cmask = __ballot_sync(0xffffffffu, compute);
         __syncwarp();
         if (cmask) {
@@ -1160,8 +1212,16 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
           const unsigned nnb = nnb_s[lane], ncont = nct_s[lane];
           c_nbr += nnb;
           c_cont += ncont;
+          double px = 0.0, py = 0.0, pz = 0.0;
+          if (MODE == FM_STEP) {
+            // P_t, copied to shared memory asynchronously at the group's start
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            px = pos_s[lane];
+            py = pos_s[32 + lane];
+            pz = pos_s[64 + lane];
+          }
           finish_agent<1, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, t.x, t.y, t.z, 0.0, 0.0, 0.0,
-                                nnb, ncont, c_static, c_moved, s_bb[warp]);
+                                nnb, ncont, c_static, c_moved, s_bb[warp], px, py, pz);
         }
       }
     }
