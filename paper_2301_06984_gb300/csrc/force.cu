@@ -418,6 +418,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ int s_nocc[27];
   __shared__ unsigned long long s_ndirty[27];
   __shared__ int s_next;
+  __shared__ unsigned s_bcnt[64];
+  __shared__ uint8_t s_order[64];
   __shared__ long long s_o;
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[FORCE_WARPS][6];
@@ -471,6 +473,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       s_nocc[t] = occ;
       s_ndirty[t] = dm;
     }
+    if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
@@ -480,12 +483,25 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       continue;
     const double dt = G.dt;
     const float dt_f = G.dt_f;
+    // the warps take the brick's boxes heaviest first (fewest idle warps at
+    // the brick's end): rank by agent count, ties by box index
+    if (threadIdx.x < 64) {
+      const unsigned c = s_bcnt[threadIdx.x];
+      unsigned r = 0;
+      for (int q = 0; q < 64; ++q) {
+        const unsigned cq = s_bcnt[q];
+        r += (cq > c) || (cq == c && q < (int)threadIdx.x);
+      }
+      s_order[r] = (uint8_t)threadIdx.x;
+    }
+    __syncthreads();
 
     while (true) {
-      int lb = 0;
-      if (lane == 0) lb = atomicAdd(&s_next, 1);
-      lb = __shfl_sync(0xffffffffu, lb, 0);
-      if (lb >= 64) break;
+      int kb = 0;
+      if (lane == 0) kb = atomicAdd(&s_next, 1);
+      kb = __shfl_sync(0xffffffffu, kb, 0);
+      if (kb >= 64) break;
+      const int lb = s_order[kb];
       const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
       if (nq == 0) continue;
       int lx, ly, lz;
@@ -883,6 +899,8 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   __shared__ int s_nocc[27];
   __shared__ unsigned long long s_ndirty[27];
   __shared__ int s_next;
+  __shared__ unsigned s_bcnt[64];
+  __shared__ uint8_t s_order[64];
   __shared__ long long s_o;
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[F32_WARPS][6];
@@ -943,6 +961,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       s_nocc[t] = occ;
       s_ndirty[t] = dm;
     }
+    if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
@@ -952,12 +971,25 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       continue;
     const double dt = G.dt;
     const float dt_f = G.dt_f;
+    // the warps take the brick's boxes heaviest first (fewest idle warps at
+    // the brick's end): rank by agent count, ties by box index
+    if (threadIdx.x < 64) {
+      const unsigned c = s_bcnt[threadIdx.x];
+      unsigned r = 0;
+      for (int q = 0; q < 64; ++q) {
+        const unsigned cq = s_bcnt[q];
+        r += (cq > c) || (cq == c && q < (int)threadIdx.x);
+      }
+      s_order[r] = (uint8_t)threadIdx.x;
+    }
+    __syncthreads();
 
     while (true) {
-      int lb = 0;
-      if (lane == 0) lb = atomicAdd(&s_next, 1);
-      lb = __shfl_sync(0xffffffffu, lb, 0);
-      if (lb >= 64) break;
+      int kb = 0;
+      if (lane == 0) kb = atomicAdd(&s_next, 1);
+      kb = __shfl_sync(0xffffffffu, kb, 0);
+      if (kb >= 64) break;
+      const int lb = s_order[kb];
       const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
       if (nq == 0) continue;
       int lx, ly, lz;
