@@ -17,6 +17,8 @@
 // to the FP64 oracle.  Both forms decide "neighbour" (d^2 < R^2) and
 // "contact" (delta > 0) exactly as FP64 does: an FP32 estimate with a rigorous
 // error band decides outside the band, FP64 decides inside it.
+#include <type_traits>
+
 #include "bdm_internal.cuh"
 
 namespace {
@@ -1190,23 +1192,29 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
                 q = ag[a];
                 own = own0 + a - cstart;
               }
-              // eight candidate blocks of agent a per step (independent chains)
-              unsigned bal[8];
+              // eight (or, for the last few, four) candidate blocks of agent a
+              // per step: independent chains
+              auto scan_step = [&](auto width) {
+                constexpr int NW = decltype(width)::value;
+                unsigned bal[NW];
 #pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                const unsigned i = (b + u) * 32u + (unsigned)lane;
-                const float4 c = sc[min(i, (unsigned)F32_CHUNK - 1u)];
-                const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                bal[u] = __ballot_sync(0xffffffffu, i < fill && d2 < P.R2_hi_f && i != own);
-              }
+                for (int u = 0; u < NW; ++u) {
+                  const unsigned i = (b + u) * 32u + (unsigned)lane;
+                  const float4 c = sc[min(i, (unsigned)F32_CHUNK - 1u)];
+                  const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
+                  const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                  bal[u] = __ballot_sync(0xffffffffu, i < fill && d2 < P.R2_hi_f && i != own);
+                }
 #pragma unroll
-              for (int u = 0; u < 8; ++u) {
-                if ((bal[u] >> lane) & 1u)
-                  ring[(tail + (unsigned)__popc(bal[u] & lt_mask)) & (F32_RING - 1)] = (a << 16) | ((b + u) * 32u + lane);
-                tail += (unsigned)__popc(bal[u]);
-              }
-              b += 8;
+                for (int u = 0; u < NW; ++u) {
+                  if ((bal[u] >> lane) & 1u)
+                    ring[(tail + (unsigned)__popc(bal[u] & lt_mask)) & (F32_RING - 1)] = (a << 16) | ((b + u) * 32u + lane);
+                  tail += (unsigned)__popc(bal[u]);
+                }
+                b += NW;
+              };
+              if (nblk - b > 4u) scan_step(std::integral_constant<int, 8>());
+              else scan_step(std::integral_constant<int, 4>());
               if (b >= nblk) {
                 b = 0;
                 am &= am - 1;
