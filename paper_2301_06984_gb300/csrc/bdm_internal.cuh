@@ -92,6 +92,7 @@ struct DevCounters {
   // FORCE_HEAVY_HI agents (heavy list front), then of at least FORCE_HEAVY_LO
   // (heavy list back), then the rest in Morton order
   unsigned long long heavy_n[2], heavy_take[2];
+  unsigned long long work_n;     // entries of the static pass's work list
   // per-iteration accumulators (reset by the geometry kernel)
   unsigned long long a_static, a_moved, a_cand, a_nbr, a_contact, a_exact;
   // snapshot of the last completed iteration
@@ -146,6 +147,8 @@ struct DevBufs {
   long long *nbr_out;
   int32_t *dbg_i32;               // debug: contacts / neighbours
   int32_t *heavy;                 // occ_cap: occupied indices of heavy bricks (both ends)
+  unsigned long long *need;       // occ_cap: boxes with non-static agents (static pass)
+  int32_t *worklist;              // occ_cap: light bricks with work left (static pass)
   float4 *defer_c;                // FP32-form deferred pairs: contribution, bound
   uint2 *defer_w;                 // FP32-form deferred pairs: index, agent | kind
   long long brick_cap, occ_cap, cap, nbr_cap;

@@ -68,7 +68,7 @@ enum Phase { PH_GEOMETRY, PH_BRICK_RANK, PH_KEYS, PH_BRICK_SCAN, PH_SCATTER, PH_
              PH_DIVIDE, PH_FINISH, PH_COUNT };
 static const char *kPhaseNames[PH_COUNT] = {"geometry", "brick_rank", "keys", "brick_scan", "scatter",
                                             "brick_sort", "gather", "force", "divide", "finish"};
-static const int kPhaseLaunches[PH_COUNT] = {1, 1, 1, 3, 1, 1, 2, 2, 3, 1};
+static const int kPhaseLaunches[PH_COUNT] = {1, 1, 1, 3, 1, 2, 2, 2, 3, 1};
 
 // ------------------------------------------------------------------ helpers
 static int fail(bdm_sim *s, int code, const std::string &msg) {
@@ -205,6 +205,8 @@ static int alloc_grid(bdm_sim *s, long long brick_cap, long long occ_cap) {
   A((void **)&B.occ_list, sizeof(int32_t) * occ_cap);
   A((void **)&B.occ_info, sizeof(int4) * occ_cap);
   A((void **)&B.heavy, sizeof(int32_t) * occ_cap);
+  A((void **)&B.need, sizeof(unsigned long long) * occ_cap);
+  A((void **)&B.worklist, sizeof(int32_t) * occ_cap);
   A((void **)&B.box_start, sizeof(uint32_t) * occ_cap * 64);
   A((void **)&B.box_cnt, sizeof(uint32_t) * occ_cap * 64);
   A((void **)&B.scan_a, sizeof(uint32_t) * scan_n);
@@ -318,6 +320,7 @@ static long long kernels_per_step(const bdm_sim *s) {
   long long k = 0;
   for (int p = 0; p < PH_COUNT; ++p)
     if (p != PH_DIVIDE || s->dp.grow) k += kPhaseLaunches[p];
+  if (s->dp.detect_static) k += 1;  // the static pass before the force kernel
   return k;
 }
 

@@ -228,53 +228,27 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 // that thread's cursor, starting at 0): the heaviest bricks first, so that no
 // CTA starts a dense brick when the others are about to run out of work.
 // Returns -1 when every brick has been handed out.
-__device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCounters *C, long long n_occ, int &phase) {
+// With static detection (use_static) only bricks with work left after
+// k_static are handed out: heavy ones whose need mask is not empty, then the
+// work list.
+__device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCounters *C, long long n_occ, int &phase,
+                                                      bool use_static) {
   while (true) {
     if (phase < 2) {
       const unsigned long long u = atomicAdd(&C->heavy_take[phase], 1ull);
-      if (u < C->heavy_n[phase]) return phase == 0 ? B.heavy[u] : B.heavy[B.occ_cap - 1 - (long long)u];
+      if (u < C->heavy_n[phase]) {
+        const long long o = phase == 0 ? B.heavy[u] : B.heavy[B.occ_cap - 1 - (long long)u];
+        if (!use_static || B.need[o]) return o;
+        continue;
+      }
       phase++;
       continue;
     }
-    const long long o = (long long)atomicAdd(&C->work_next, 1ull);
-    if (o >= n_occ) return -1;
-    if (B.brick_count[B.occ_list[o]] < FORCE_HEAVY_LO) return o;  // heavy ones were listed
+    const long long u = (long long)atomicAdd(&C->work_next, 1ull);
+    if (use_static) return u < (long long)C->work_n ? (long long)B.worklist[u] : -1;
+    if (u >= n_occ) return -1;
+    if (B.brick_count[B.occ_list[u]] < FORCE_HEAVY_LO) return u;  // heavy ones were listed
   }
-}
-
-// Static-brick pass (FM_STEP with static detection; called by the whole CTA
-// once s_ndirty holds the masks of the brick and its 26 neighbours).  When no
-// box there is dirty, an agent of the brick is static exactly when it did not
-// change in the previous iteration and had at most one contact; if all of
-// them are, the CTA finishes the brick as one streaming pass over its agents
-// (flag, bounding box, zero force), with the result the per-box path gives a
-// static agent, and returns true.  Otherwise it returns false.
-__device__ bool static_brick_pass(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, long long o,
-                                  const unsigned long long *s_ndirty, unsigned &c_static,
-                                  unsigned long long *bb_w) {
-  const int clean = (threadIdx.x < 27) ? (s_ndirty[threadIdx.x] == 0ull) : 1;
-  if (!__syncthreads_and(clean)) return false;
-  const int g = B.occ_list[o];
-  const unsigned S0 = B.brick_start[g], m = B.brick_count[g];
-  int all = 1;
-  for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-    const uint32_t iq = B.perm[S0 + k];
-    all &= !(A.flags[iq] & FL_CHANGED) && A.nz[iq] <= 1;
-  }
-  if (!__syncthreads_and(all)) return false;
-  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
-  for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-    const uint32_t iq = B.perm[S0 + k];
-    if (A.flags[iq] != FL_STATIC) A.flags[iq] = FL_STATIC;
-    const unsigned long long e[3] = {enc_f64(A.x[cur][iq]), enc_f64(A.y[cur][iq]), enc_f64(A.z[cur][iq])};
-    for (int d = 0; d < 3; ++d) { mn[d] = min(mn[d], e[d]); mx[d] = max(mx[d], e[d]); }
-    if (P.keep_forces) { B.fdbg[iq] = 0.0; B.fdbg[B.cap + iq] = 0.0; B.fdbg[2 * B.cap + iq] = 0.0; }
-    c_static++;
-  }
-  for (int d = 0; d < 3; ++d) { mn[d] = wmin64(mn[d]); mx[d] = wmax64(mx[d]); }
-  if ((threadIdx.x & 31) == 0 && mn[0] != ~0ull)
-    for (int d = 0; d < 3; ++d) { atomicMin(&bb_w[d], mn[d]); atomicMax(&bb_w[3 + d], mx[d]); }
-  return true;
 }
 
 // flush a warp's shared bounding-box accumulator into the simulation's
@@ -422,6 +396,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ int s_next;
   __shared__ unsigned s_bcnt[64];
   __shared__ uint8_t s_order[64];
+  __shared__ unsigned long long s_need;
   __shared__ long long s_o;
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[FORCE_WARPS][6];
@@ -454,7 +429,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = next_force_brick(B, C, n_occ, fetch_phase);
+      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
       s_next = 0;
     }
     __syncthreads();
@@ -476,13 +451,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       s_ndirty[t] = dm;
     }
     if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
+    if (threadIdx.x == 128) s_need = use_static ? B.need[o] : ~0ull;
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
-    if (MODE == FM_STEP && use_static && static_brick_pass(B, P, A, cur, o, s_ndirty, c_static, s_bb[warp]))
-      continue;
+
     const double dt = G.dt;
     const float dt_f = G.dt_f;
     // the warps take the brick's boxes heaviest first (fewest idle warps at
@@ -504,6 +479,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       kb = __shfl_sync(0xffffffffu, kb, 0);
       if (kb >= 64) break;
       const int lb = s_order[kb];
+      if (!((s_need >> lb) & 1ull)) continue;  // nothing left after the static pass
       const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
       if (nq == 0) continue;
       int lx, ly, lz;
@@ -777,6 +753,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         c_cont += ncont;
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
+        if (is_static) continue;  // finished by the static pass
         double px = 0.0, py = 0.0, pz = 0.0;
         if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
         finish_agent<PREC, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, ffx, ffy, ffz, dfx, dfy, dfz,
@@ -871,6 +848,108 @@ __device__ __noinline__ unsigned settle_deferred(ExactSrc X, unsigned kq0, unsig
   return n_exact;
 }
 
+// ---------------------------------------------------------------- static pass
+// Static agents (FM_STEP with static detection, before the force kernel).  A
+// box is clean when no box of its 27-box stencil is dirty; an agent of a clean
+// box that did not change in the previous iteration and had at most one
+// contact is static.  One warp per occupied brick finishes the brick's static
+// agents in a streaming pass (flag, bounding box, zero force: what the per-box
+// path does for a static agent) and stores in need[o] the brick's boxes that
+// still hold non-static agents; bricks with such boxes and fewer than
+// FORCE_HEAVY_LO agents go to the work list the force kernel takes them from
+// (heavier ones stay on the heavy lists).  High occupancy hides the per-brick
+// latency that a force-kernel block would serialise.
+#define KS_WARPS 8
+__global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P) {
+  __shared__ unsigned long long s_dm[KS_WARPS][27];
+  __shared__ unsigned s_bst[KS_WARPS][64], s_bcnt[KS_WARPS][64], s_work[KS_WARPS][64];
+  DevCounters *C = B.ctr;
+  if (C->error || !(P.detect_static && C->history_valid)) return;
+  const AgentSet &A = *B.A;
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const long long n_occ = C->n_occ;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned c_static = 0;
+  unsigned long long mn[3] = {~0ull, ~0ull, ~0ull}, mx[3] = {0ull, 0ull, 0ull};
+  int wsim = -1;
+  auto flush = [&]() {
+    unsigned long long v[6];
+    for (int d = 0; d < 3; ++d) { v[d] = wmin64(mn[d]); v[3 + d] = wmax64(mx[d]); mn[d] = ~0ull; mx[d] = 0ull; }
+    if (lane == 0 && wsim >= 0 && v[0] != ~0ull) {
+      unsigned long long *bb = B.bbox + ((size_t)nxt * P.n_sims + wsim) * 6;
+      for (int d = 0; d < 3; ++d) { atomicMin(&bb[d], v[d]); atomicMax(&bb[3 + d], v[3 + d]); }
+    }
+  };
+  for (long long o = (long long)blockIdx.x * KS_WARPS + w; o < n_occ; o += (long long)gridDim.x * KS_WARPS) {
+    const int4 info = B.occ_info[o];
+    if (info.w != wsim) {
+      flush();
+      wsim = info.w;
+    }
+    const SimGeom &G = B.geom[info.w];
+    if (lane < 27) {
+      const int X = info.x + lane % 3 - 1, Y = info.y + (lane / 3) % 3 - 1, Z = info.z + lane / 9 - 1;
+      unsigned long long dm = 0ull;
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2])
+        dm = B.dirty[B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X]];
+      s_dm[w][lane] = dm;
+    }
+    s_bst[w][lane] = B.box_start[o * 64 + lane];
+    s_bst[w][lane + 32] = B.box_start[o * 64 + lane + 32];
+    s_bcnt[w][lane] = B.box_cnt[o * 64 + lane];
+    s_bcnt[w][lane + 32] = B.box_cnt[o * 64 + lane + 32];
+    __syncwarp();
+    // clean boxes (the per-box path's stencil test), lane and lane + 32
+    unsigned long long cm = 0ull;
+    for (int h = 0; h < 2; ++h) {
+      const int lb = lane + 32 * h;
+      int lx, ly, lz;
+      local_decode(lb, lx, ly, lz);
+      bool dirty = false;
+      for (int t = 0; t < 27; ++t) {
+        const int ax = lx + t % 3 - 1, ay = ly + (t / 3) % 3 - 1, az = lz + t / 9 - 1;
+        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+        dirty |= ((s_dm[w][bo] >> local_code(ax & 3, ay & 3, az & 3)) & 1ull) != 0ull;
+      }
+      s_work[w][lb] = dirty ? s_bcnt[w][lb] : 0u;
+      cm |= (unsigned long long)__ballot_sync(0xffffffffu, !dirty) << (32 * h);
+    }
+    __syncwarp();
+    const unsigned S0 = s_bst[w][0], m = s_bst[w][63] + s_bcnt[w][63] - S0;
+    for (unsigned k = lane; k < m; k += 32) {
+      // the box holding sorted position S0 + k: the last one starting at or
+      // before it (an empty box starts where the next one does)
+      int lb = 0;
+      for (int st = 32; st > 0; st >>= 1)
+        if (lb + st < 64 && s_bst[w][lb + st] <= S0 + k) lb += st;
+      if (!((cm >> lb) & 1ull)) continue;
+      const uint32_t iq = B.perm[S0 + k];
+      const uint8_t fl = A.flags[iq];
+      if ((fl & FL_CHANGED) || A.nz[iq] > 1) {
+        atomicAdd(&s_work[w][lb], 1u);
+        continue;
+      }
+      if (fl != FL_STATIC) A.flags[iq] = FL_STATIC;
+      const unsigned long long e[3] = {enc_f64(A.x[cur][iq]), enc_f64(A.y[cur][iq]), enc_f64(A.z[cur][iq])};
+      for (int d = 0; d < 3; ++d) { mn[d] = min(mn[d], e[d]); mx[d] = max(mx[d], e[d]); }
+      if (P.keep_forces) { B.fdbg[iq] = 0.0; B.fdbg[B.cap + iq] = 0.0; B.fdbg[2 * B.cap + iq] = 0.0; }
+      c_static++;
+    }
+    __syncwarp();
+    const unsigned long long need = (unsigned long long)__ballot_sync(0xffffffffu, s_work[w][lane] > 0u) |
+                                    ((unsigned long long)__ballot_sync(0xffffffffu, s_work[w][lane + 32] > 0u) << 32);
+    if (lane == 0) {
+      B.need[o] = need;
+      if (need && m < FORCE_HEAVY_LO) B.worklist[atomicAdd(&C->work_n, 1ull)] = (int32_t)o;
+    }
+    __syncwarp();
+  }
+  flush();
+  const unsigned long long t = wsum64(c_static);
+  if (lane == 0 && t) atomicAdd(&C->a_static, t);
+}
+
 // ---------------------------------------------------------------- FP32 form: pair-ring kernel
 // The FP32 form's production kernel.  Same work decomposition as k_force
 // (one CTA per occupied brick, one warp per box), but the pairs are not
@@ -903,6 +982,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   __shared__ int s_next;
   __shared__ unsigned s_bcnt[64];
   __shared__ uint8_t s_order[64];
+  __shared__ unsigned long long s_need;
   __shared__ long long s_o;
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[F32_WARPS][6];
@@ -942,7 +1022,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = next_force_brick(B, C, n_occ, fetch_phase);
+      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
       s_next = 0;
     }
     __syncthreads();
@@ -964,13 +1044,13 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       s_ndirty[t] = dm;
     }
     if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
+    if (threadIdx.x == 128) s_need = use_static ? B.need[o] : ~0ull;
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
-    if (MODE == FM_STEP && use_static && static_brick_pass(B, P, A, cur, o, s_ndirty, c_static, s_bb[warp]))
-      continue;
+
     const double dt = G.dt;
     const float dt_f = G.dt_f;
     // the warps take the brick's boxes heaviest first (fewest idle warps at
@@ -992,6 +1072,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       kb = __shfl_sync(0xffffffffu, kb, 0);
       if (kb >= 64) break;
       const int lb = s_order[kb];
+      if (!((s_need >> lb) & 1ull)) continue;  // nothing left after the static pass
       const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
       if (nq == 0) continue;
       int lx, ly, lz;
@@ -1037,7 +1118,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
         bnd[lane] = 0.f;
         nnb_s[lane] = 0u;
         nct_s[lane] = 0u;
-        if (MODE == FM_STEP && valid) {
+        if (MODE == FM_STEP && valid && !is_static) {
           // the epilogue's P_t, fetched while the pairs are evaluated
           const unsigned sa = (unsigned)__cvta_generic_to_shared(pos_s + lane);
           asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(A.x[cur] + iq) : "memory");
@@ -1247,7 +1328,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
                                        qbase + q0, dlen, rmask, dc, dw, acc, bnd, nnb_s, nct_s);
           }
         }
-        if (valid) {
+        if (valid && !is_static) {  // static agents were finished by the static pass
           const float4 t = acc[lane];
           const unsigned nnb = nnb_s[lane], ncont = nct_s[lane];
           c_nbr += nnb;
@@ -1266,6 +1347,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       }
     }
   }
+  if (MODE == FM_STEP) asm volatile("cp.async.wait_all;\n" ::: "memory");  // none left in flight at exit
   if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
   const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = wsum64(c_cand),
                            t_nbr = wsum64(c_nbr), t_cont = wsum64(c_cont), t_exact = wsum64(c_exact);
@@ -1435,6 +1517,7 @@ __global__ void k_nbr_offsets(DevBufs B) {
 
 void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
   k_reset_work<<<1, 1, 0, s>>>(B);
+  if (mode == FM_STEP && P.detect_static) k_static<<<2 * c.occ_blocks, KS_WARPS * 32, 0, s>>>(B, P);
   if (P.precision == 1 && P.lanes_fixed == 0 && (mode == FM_STEP || mode == FM_FORCES)) {
     // the FP32 form's pair-ring kernel (dynamic shared memory above 48 KB)
     constexpr int smem = F32_WARPS * F32_WARP_SMEM;

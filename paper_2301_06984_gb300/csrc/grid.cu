@@ -201,6 +201,7 @@ __global__ void k_geometry(DevBufs B, DevParams P) {
     C->max_brick = 0;
     C->n_occ = 0;
     C->heavy_n[0] = C->heavy_n[1] = 0;
+    C->work_n = 0;
     C->sort_now = ((P.sort_every > 0 && (C->step % P.sort_every) == 0) || C->force_sort) ? 1 : 0;
     C->force_sort = 0;
   }
@@ -399,6 +400,12 @@ __global__ void k_scatter(DevBufs B) {
 
 // --------------------------------------------------------------- brick sort
 #define BS_THREADS 256
+
+// Bricks of at most BSW_MAX agents (most bricks of sparse workloads) are
+// sorted by k_brick_sort_small, one warp per brick, with the same result;
+// k_brick_sort takes the rest, one block per brick.
+#define BSW_MAX 128
+#define BSW_WARPS 8
 #define BS_SMEM_M 4096
 
 // box-local compact record of agent i in its box (bx, by, bz)
@@ -424,6 +431,23 @@ __device__ __forceinline__ void write_compact(const DevBufs &B, const DevParams 
   B.c32[k] = make_float4(xl, yl, zl, r);
 }
 
+// Agent idx at sorted position kk of occupied brick o: its storage index, its
+// box-local compact record and, for the brick's first agent, the brick's
+// coordinates and simulation.
+__device__ __forceinline__ void place_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
+                                            long long o, uint32_t idx, long long kk, bool first) {
+  B.perm[kk] = idx;
+  const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, idx);
+  const SimGeom &G = B.geom[s];
+  const double x = A.x[cur][idx], y = A.y[cur][idx], z = A.z[cur][idx];
+  bool fb;
+  int bx = min(max(box_axis(x, G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
+  int by = min(max(box_axis(y, G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
+  int bz = min(max(box_axis(z, G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
+  write_compact(B, P, A, cur, G, idx, kk, bx, by, bz, x, y, z);
+  if (first) B.occ_info[o] = make_int4(bx >> 2, by >> 2, bz >> 2, s);
+}
+
 __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams P) {
   __shared__ uint32_t s_idx[BS_SMEM_M];
   __shared__ uint32_t s_grp[BS_SMEM_M];
@@ -440,6 +464,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
     const int g = B.occ_list[o];
     const unsigned S0 = B.brick_start[g];
     const unsigned m = B.brick_count[g];
+    if (m <= BSW_MAX) continue;  // block-uniform: k_brick_sort_small's brick
     const bool onchip = m <= BS_SMEM_M;
     if (threadIdx.x == 0 && m >= FORCE_HEAVY_LO) {
       // heavy bricks, listed for the force kernels' largest-first order
@@ -503,22 +528,78 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
       } else {
         for (unsigned q = 0; q < cnt; ++q) r += (B.arrival[S0 + lo + q] < idx);
       }
-      const long long kk = (long long)S0 + lo + r;
-      B.perm[kk] = idx;
-      const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, idx);
-      const SimGeom &G = B.geom[s];
-      const double x = A.x[cur][idx], y = A.y[cur][idx], z = A.z[cur][idx];
-      bool fb;
-      int bx = min(max(box_axis(x, G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
-      int by = min(max(box_axis(y, G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
-      int bz = min(max(box_axis(z, G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
-      write_compact(B, P, A, cur, G, idx, kk, bx, by, bz, x, y, z);
-      if (lo + r == 0) B.occ_info[o] = make_int4(bx >> 2, by >> 2, bz >> 2, s);
+      place_agent(B, P, A, cur, o, idx, (long long)S0 + lo + r, lo + r == 0);
     }
     if (threadIdx.x < 64) {
       B.box_start[o * 64 + threadIdx.x] = S0 + s_off[threadIdx.x];
       B.box_cnt[o * 64 + threadIdx.x] = s_cnt[threadIdx.x];
     }
+  }
+}
+
+// One warp per brick of at most BSW_MAX agents: per-box counts (shared
+// atomics), exclusive scan of the 64 counts, grouping by box, then the stable
+// rank inside each box by storage index, exactly as k_brick_sort.
+__global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, DevParams P) {
+  __shared__ uint32_t s_idx[BSW_WARPS][BSW_MAX], s_grp[BSW_WARPS][BSW_MAX];
+  __shared__ uint8_t s_l[BSW_WARPS][BSW_MAX], s_gl[BSW_WARPS][BSW_MAX];
+  __shared__ unsigned s_cnt[BSW_WARPS][64], s_off[BSW_WARPS][64], s_cur[BSW_WARPS][64];
+  const DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1);
+  const long long n_occ = C->n_occ;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nw = (long long)gridDim.x * BSW_WARPS;
+  for (long long o = (long long)blockIdx.x * BSW_WARPS + w; o < n_occ; o += nw) {
+    const int g = B.occ_list[o];
+    const unsigned S0 = B.brick_start[g], m = B.brick_count[g];
+    if (m > BSW_MAX) continue;  // warp-uniform: k_brick_sort's brick
+    s_cnt[w][lane] = 0u;
+    s_cnt[w][lane + 32] = 0u;
+    __syncwarp();
+    for (unsigned k = lane; k < m; k += 32) {
+      const uint32_t idx = B.bucket[S0 + k];
+      const unsigned l = B.key[idx] & 63u;
+      s_idx[w][k] = idx;
+      s_l[w][k] = (uint8_t)l;
+      atomicAdd(&s_cnt[w][l], 1u);
+    }
+    __syncwarp();
+    {
+      const unsigned a = s_cnt[w][lane], b = s_cnt[w][lane + 32];
+      unsigned xa = a, xb = b;
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned ya = __shfl_up_sync(0xffffffffu, xa, d), yb = __shfl_up_sync(0xffffffffu, xb, d);
+        if (lane >= d) { xa += ya; xb += yb; }
+      }
+      const unsigned ta = __shfl_sync(0xffffffffu, xa, 31);
+      s_off[w][lane] = s_cur[w][lane] = xa - a;
+      s_off[w][lane + 32] = s_cur[w][lane + 32] = ta + xb - b;
+    }
+    __syncwarp();
+    // group by box (arrival order inside a group)
+    for (unsigned k = lane; k < m; k += 32) {
+      const unsigned l = s_l[w][k];
+      const unsigned pos = atomicAdd(&s_cur[w][l], 1u);
+      s_grp[w][pos] = s_idx[w][k];
+      s_gl[w][pos] = (uint8_t)l;
+    }
+    __syncwarp();
+    // stable rank inside the box = members with a smaller storage index
+    for (unsigned k = lane; k < m; k += 32) {
+      const uint32_t idx = s_grp[w][k];
+      const unsigned l = s_gl[w][k];
+      const unsigned lo = s_off[w][l], cnt = s_cnt[w][l];
+      unsigned r = 0;
+      for (unsigned q = 0; q < cnt; ++q) r += (s_grp[w][lo + q] < idx);
+      place_agent(B, P, A, cur, o, idx, (long long)S0 + lo + r, lo + r == 0);
+    }
+    B.box_start[o * 64 + lane] = S0 + s_off[w][lane];
+    B.box_start[o * 64 + lane + 32] = S0 + s_off[w][lane + 32];
+    B.box_cnt[o * 64 + lane] = s_cnt[w][lane];
+    B.box_cnt[o * 64 + lane + 32] = s_cnt[w][lane + 32];
+    __syncwarp();
   }
 }
 
@@ -693,6 +774,7 @@ void launch_scatter(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cu
   k_scatter<<<c.agent_blocks, 256, 0, s>>>(B);
 }
 void launch_brick_sort(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  k_brick_sort_small<<<c.occ_blocks, BSW_WARPS * 32, 0, s>>>(B, P);
   k_brick_sort<<<c.occ_blocks, BS_THREADS, 0, s>>>(B, P);
 }
 void launch_gather(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
