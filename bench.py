@@ -397,7 +397,7 @@ def main():
     traffic, sha = committed_traffic()
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    roofline = {"bound": "alu", "kernel": "k_force32<STEP> (FP32 pair-ring force kernel)", "achieved": achieved, "peak": peak_alu,
+    roofline = {"bound": "alu", "kernel": "k_force<FP32,STEP> (lane-per-agent force kernel, 4 lanes per agent)", "achieved": achieved, "peak": peak_alu,
                 "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal, derived)",
                 "flops_per_launch": flops,

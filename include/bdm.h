@@ -195,9 +195,10 @@ int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out
 /* Autotuner.  Times `trial_steps` iterations of the production path (after
  * one warm-up iteration) for each candidate setting, restoring the state
  * before every trial, and keeps the fastest: the box edge L in {R, 1.125 R,
- * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel in {pair-ring
- * kernel, lane-per-agent kernel with 1, 2 or 4 lanes per agent}
- * (BDM_TUNE_LANES), and the sort
+ * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel in {lane-per-agent
+ * kernel with 4 lanes per agent, pair-ring kernel, lane-per-agent kernel with
+ * the per-box cost model, with 2 lanes, with 8 lanes} (BDM_TUNE_LANES; the
+ * values of bdm_set_force_kernel), and the sort
  * cadence in {current, 0, 5, 10, 20} (BDM_TUNE_SORT), one dimension after the
  * other.  The state (agents, step, uid counter) is the same afterwards; the
  * static-detection history starts empty.  Changing L keeps neighbour sets
@@ -209,8 +210,7 @@ int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out
 typedef struct {
   double box_edge;     /* chosen L (um)                                     */
   double ms_per_step;  /* measured time per iteration of the chosen setting */
-  int32_t lanes;       /* 0 = pair-ring kernel, else lanes per agent of the
-                          lane-per-agent kernel                              */
+  int32_t lanes;       /* FP32 kernel choice, as in bdm_set_force_kernel    */
   int32_t sort_every;  /* chosen sort cadence                               */
   int32_t n_trials;    /* settings timed                                    */
   int32_t reserved;
@@ -218,14 +218,16 @@ typedef struct {
 int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
 
 /* FP32-force kernel choice (no counterpart in the paper, whose force loop is
- * one thread per agent).  lanes = 0 selects the pair-ring kernel (the
- * default): per box the warp tests 32 candidates per instruction, queues the
- * pairs inside the cutoff band and evaluates them 32 at a time.  lanes = 1,
- * 2, 4, 8, 16 or 32 selects the lane-per-agent kernel with that many lanes
- * splitting each agent's candidates.  Both give the same neighbour and
- * contact decisions (FP64-exact) and forces within the FP32-form tolerance;
- * the choice takes effect at the next iteration.  No effect on the FP64
- * form.  Errors: BDM_EINVAL (other lanes values). */
+ * one thread per agent).  lanes = 1, 2, 4 (the default), 8, 16 or 32 selects
+ * the lane-per-agent kernel: a warp takes a box's agents, that many lanes
+ * split each agent's candidates, and each lane queues its prefiltered pairs
+ * before evaluating them.  lanes = -1 selects the same kernel with the lanes
+ * chosen per box by a cost model.  lanes = 0 selects the pair-ring kernel: per
+ * box the warp tests 32 candidates per instruction, queues the pairs inside
+ * the cutoff band and evaluates them 32 at a time.  All give the same
+ * neighbour and contact decisions (FP64-exact) and forces within the
+ * FP32-form tolerance; the choice takes effect at the next iteration.  No
+ * effect on the FP64 form.  Errors: BDM_EINVAL (other lanes values). */
 int bdm_set_force_kernel(bdm_sim *sim, int lanes);
 
 /* Phase profiling.  After bdm_profile_begin, bdm_step launches each

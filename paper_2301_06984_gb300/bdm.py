@@ -295,9 +295,10 @@ class Simulation:
         self._check(lib().bdm_autotune(self._h, int(trial_steps), int(what), C.byref(t)))
         return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
 
-    def set_force_kernel(self, lanes=0):
-        """FP32 form: 0 = pair-ring kernel, else lanes per agent of the
-        lane-per-agent kernel (1, 2, 4, 8, 16 or 32)."""
+    def set_force_kernel(self, lanes=4):
+        """FP32 form: lanes per agent of the lane-per-agent kernel (1, 2, 4 =
+        default, 8, 16, 32; -1 = chosen per box by its cost model), or 0 for
+        the pair-ring kernel."""
         self._check(lib().bdm_set_force_kernel(self._h, int(lanes)))
 
     # ------------------------------------------------------------------ profiling

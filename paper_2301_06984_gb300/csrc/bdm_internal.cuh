@@ -115,8 +115,9 @@ struct DevParams {
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk;
-  int32_t lanes_fixed;              // FP32 form: 0 = pair-ring kernel (k_force32), else
-                                    // lanes per agent of the lane-per-agent kernel (k_force)
+  int32_t lanes_fixed;              // FP32 form: 0 = pair-ring kernel (k_force32); > 0 lanes
+                                    // per agent of the lane-per-agent kernel (k_force); -1 that
+                                    // kernel with lanes chosen per box by its cost model
 };
 
 // Everything a kernel reaches, passed by value.
@@ -249,6 +250,10 @@ struct LaunchCfg {
   int force_blocks;    // k_force (FP64 form, neighbour modes, fixed lanes per agent)
   int force32_blocks;  // k_force32 (FP32 form)
 };
+
+// default FP32 force kernel: the lane-per-agent kernel with 4 lanes per agent
+// (fastest of the choices on the dense and the static-core workloads)
+#define FORCE_LANES_DEFAULT 4
 
 // brick weight classes of the force kernels' largest-first order (agents)
 #define FORCE_HEAVY_HI 1024

@@ -158,6 +158,7 @@ static DevParams make_dev_params(const bdm_params &P) {
   d.abs_tol = 1e-6f;
   d.cband1 = (float)(4.0 * std::sqrt(3.0) * E);
   d.cband2 = (float)(10.0 * pow2i(-23));
+  d.lanes_fixed = FORCE_LANES_DEFAULT;
   d.kf = (float)P.k;
   d.gammaf = (float)P.gamma;
   d.dmaxf = (float)P.max_displacement;
@@ -784,8 +785,9 @@ static int apply_params(bdm_sim *s, const bdm_params &P, int lanes) {
 
 int bdm_set_force_kernel(bdm_sim *s, int lanes) {
   if (!s) return BDM_EINVAL;
-  if (!(lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
-    return fail(s, BDM_EINVAL, "lanes must be 0, 1, 2, 4, 8, 16 or 32");
+  if (!(lanes == -1 || lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
+        lanes == 32))
+    return fail(s, BDM_EINVAL, "lanes must be -1, 0, 1, 2, 4, 8, 16 or 32");
   return apply_params(s, s->P, lanes);
 }
 
@@ -867,9 +869,9 @@ int bdm_autotune(bdm_sim *s, int trial_steps, int what, bdm_tuning *out) {
       }
     }
     if (rc == BDM_OK && (what & BDM_TUNE_LANES) && base.precision == BDM_FP32_FORCE) {
-      const int opts[4] = {0, 1, 2, 4};
+      const int opts[5] = {FORCE_LANES_DEFAULT, 0, -1, 2, 8};
       int bl = best_lanes;
-      for (int i = 0; i < 4 && rc == BDM_OK; ++i)
+      for (int i = 0; i < 5 && rc == BDM_OK; ++i)
         if ((rc = trial(best, opts[i], &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; bl = opts[i]; }
       best_lanes = bl;
     }
