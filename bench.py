@@ -57,7 +57,7 @@ def parse():
                     help="blobs: Morton re-sort cadence (0 = never; the headline workload uses 10)")
     ap.add_argument("--presort", action="store_true",
                     help="blobs: put storage in Morton order (bdm_sort) before the warm-up")
-    ap.add_argument("--no-autotune", action="store_true", help="ensemble: skip the autotuner")
+    ap.add_argument("--no-autotune", action="store_true", help="ensemble, core_shell: skip the autotuner")
     return ap.parse_args()
 
 
@@ -281,6 +281,9 @@ def run_other(args):
         w = W.core_shell()
         sim = bdm.Simulation.from_workload(w)
         sim.set_workload(w)
+        tuning = None
+        if not args.no_autotune:
+            tuning = sim.autotune(trial_steps=3)
         sim.step(args.warmup)
         c0 = sim.counters()
         ms = timed_steps(sim, args.steps, stream)
@@ -293,8 +296,9 @@ def run_other(args):
         peaks = measured_peaks()
         gbs = bytes_step / (ms / args.steps * 1e-3) / 1e9
         line.update(value=w.n * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps, dtype="f32",
-                    config={"workload": "core_shell-150M: FCC static core (90%%) + random-walk shell (10%%), "
-                                        "d = 10 um, R = L = 10 um, static-agent skip on", "n_agents": w.n},
+                    config={"workload": "core_shell-150M: FCC static core (90%) + random-walk shell (10%), "
+                                        "d = 10 um, R = 10 um, static-agent skip on", "n_agents": w.n,
+                            "autotuned": tuning},
                     skipped_fraction=st / w.n,
                     roofline={"bound": "hbm", "kernel": "whole iteration", "achieved": gbs,
                               "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
