@@ -213,10 +213,23 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- other workloads
-# algorithmic HBM bytes per agent of the FP32-form iteration, by phase (see
-# the design doc): keys 33, scatter 12, brick sort 56, force 74 (32 for a static
-# agent: its index, flags, contacts and the position read for the bounding box)
+# algorithmic HBM bytes per agent of the FP32-form iteration, by phase: keys
+# 33, scatter 12, brick sort 56, force 74 (32 for a static agent: its index,
+# flags, contacts and the position read for the bounding box)
 STEP_BYTES_MOVING, STEP_BYTES_STATIC = 33 + 12 + 56 + 74, 33 + 12 + 56 + 32
+
+
+def reduce_over_ranks(ms, updates, dist, device):
+    """Whole-job figures of a timed region: the slowest rank's time and the
+    agent-updates of all ranks (identity without a process group)."""
+    if dist is None:
+        return ms, updates
+    import torch
+    tm = torch.tensor([ms], dtype=torch.float64, device=device)
+    tu = torch.tensor([float(updates)], dtype=torch.float64, device=device)
+    dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tu, op=dist.ReduceOp.SUM)
+    return float(tm.item()), float(tu.item())
 
 
 def timed_steps(sim, k, stream):
@@ -373,13 +386,7 @@ def main():
     c1 = sim.counters()
     launches = c1["kernels_launched"] - c0["kernels_launched"]
     updates = n_before * args.steps  # no agents are added in this workload
-    t = torch.tensor([ms, float(updates)], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        tm = t[:1].clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        tu = t[1:].clone()
-        dist.all_reduce(tu, op=dist.ReduceOp.SUM)
-        ms, updates = float(tm.item()), float(tu.item())
+    ms, updates = reduce_over_ranks(ms, updates, dist, "cuda")
     value = updates / (ms * 1e-3)
 
     # ---- live per-kernel timing over a profiled pass of the same iteration
@@ -463,10 +470,8 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         mse = e0.elapsed_time(e1)
-        tt = torch.tensor([mse], dtype=torch.float64, device="cuda")
-        if dist is not None:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * n * ke / (float(tt.item()) * 1e-3), "unit": UNIT,
+        mse, upd = reduce_over_ranks(mse, n * ke, dist, "cuda")
+        line["e2e"] = {"value": upd / (mse * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 24 * n, "steps": ke}
         se.close()
 
