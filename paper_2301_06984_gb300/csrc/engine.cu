@@ -153,7 +153,21 @@ static DevParams make_dev_params(const bdm_params &P) {
   // apart and redone in FP64 when their bound is not small against the
   // agent's tolerance 2e-5 * sum(k delta + gamma sqrt(rbar delta)) + 1e-6
   d.graze = 0.2f;
-  d.graze_e = (float)(2.0 * E);
+  {
+    // error bound of an FP32 overlap delta = s - d: each component of the
+    // difference carries the conversion of both local coordinates (<= 17
+    // units of 2^-s each: truncation to fixed point, int->float rounding) and
+    // the two FP32 operations forming it (<= half an ulp of a value below
+    // 2.02 L each); d adds the rounding of d^2 (1.5 2^-24 d), rsqrtf (2 ulp)
+    // and the product d^2 rsqrt(d^2) (2^-24 d), with d below 1.01 R; a
+    // grazing pair has s = d + delta below 1.01 R + graze, and the rounding of
+    // s = r_i + r_j and of s - d adds 2^-24 (s + graze)
+    const double half_ulp = std::ldexp(1.0, (int)std::ceil(std::log2(2.02 * d.L)) - 25);
+    const double Ec = 34.0 * pow2i(-sft) + 2.0 * half_ulp;
+    const double Rm = 1.01 * R;
+    d.graze_e = (float)(std::sqrt(3.0) * Ec + (1.5 * pow2i(-24) + pow2i(-22) + pow2i(-24)) * Rm +
+                        pow2i(-24) * (Rm + 2.0 * (double)d.graze));
+  }
   d.rel_tol = 2e-5f;
   d.abs_tol = 1e-6f;
   d.cband1 = (float)(4.0 * std::sqrt(3.0) * E);
