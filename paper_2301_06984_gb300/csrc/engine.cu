@@ -596,11 +596,14 @@ int bdm_set_agents(bdm_sim *s, int64_t n, const double *xyz, const double *diam,
   const AgentSet &A = s->sets[0];
   const AgentSet &T = s->sets[1];  // staging
   if (n > 0) {
-    for (int b = 0; b < 2; ++b) {
-      CK(cudaMemcpyAsync(A.x[b], xyz, sizeof(double) * n, kind, s->own));
-      CK(cudaMemcpyAsync(A.y[b], xyz + n, sizeof(double) * n, kind, s->own));
-      CK(cudaMemcpyAsync(A.z[b], xyz + 2 * n, sizeof(double) * n, kind, s->own));
-    }
+    // P_t into both position buffers (no movement history yet): one copy
+    // from the caller, the second buffer filled on the device
+    CK(cudaMemcpyAsync(A.x[0], xyz, sizeof(double) * n, kind, s->own));
+    CK(cudaMemcpyAsync(A.y[0], xyz + n, sizeof(double) * n, kind, s->own));
+    CK(cudaMemcpyAsync(A.z[0], xyz + 2 * n, sizeof(double) * n, kind, s->own));
+    CK(cudaMemcpyAsync(A.x[1], A.x[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
+    CK(cudaMemcpyAsync(A.y[1], A.y[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
+    CK(cudaMemcpyAsync(A.z[1], A.z[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
     const double *d_diam = diam;
     const double *d_vol = nullptr;
     const uint64_t *d_uid = nullptr;
