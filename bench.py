@@ -142,7 +142,7 @@ class ClockSampler:
 # ---------------------------------------------------------------- helpers
 def force_source_sha():
     h = hashlib.sha256()
-    for f in ("force.cu", "bdm_internal.cuh", "engine.cu"):
+    for f in ("force.cu", "bdm_internal.cuh", "params.cu"):
         with open(os.path.join(ROOT, "paper_2301_06984_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libbdm_gb300.so")
-SOURCES = ["engine.cu", "grid.cu", "force.cu", "noalloc.cu"]
+SOURCES = ["engine.cu", "grid.cu", "force.cu", "noalloc.cu", "params.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "-I", CSRC, "-I", INCLUDE]

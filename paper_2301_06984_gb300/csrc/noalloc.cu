@@ -15,7 +15,7 @@
 #include "bdm_internal.cuh"
 #include "bdm.h"
 
-DevParams make_dev_params_for(const bdm_params &P);  // engine.cu
+DevParams make_dev_params_for(const bdm_params &P);  // params.cu
 
 namespace {
 
