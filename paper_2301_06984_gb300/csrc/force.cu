@@ -451,7 +451,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       s_ndirty[t] = dm;
     }
     if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
-    if (threadIdx.x == 128) s_need = use_static ? B.need[o] : ~0ull;
+    if (threadIdx.x == 32) s_need = use_static ? B.need[o] : ~0ull;
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
@@ -1044,7 +1044,7 @@ __global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B,
       s_ndirty[t] = dm;
     }
     if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
-    if (threadIdx.x == 128) s_need = use_static ? B.need[o] : ~0ull;
+    if (threadIdx.x == 32) s_need = use_static ? B.need[o] : ~0ull;
     __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
