@@ -45,10 +45,12 @@ def test_lattice_47_cubed_20_iterations_bit_exact():
 
 
 def test_blobs_10M_sampled_forces_fp32():
+    # the GPU state after iterations 1, 10 and 100; the oracle computes the
+    # forces of sampled agents from that state
     w = W.blobs()
     s = H.gpu_sim(w, precision="fp32")
     rng = np.random.default_rng(0)
-    for steps in (0, 5):
+    for steps in (1, 9, 90):
         s.step(steps)
         f_g, nz_g, nnb_g = s.forces_now()
         a, o = _state_of(s)
@@ -57,6 +59,20 @@ def test_blobs_10M_sampled_forces_fp32():
         f_o, nz_o, nnb_o, scale = o.forces_of(P, q=q, with_scale=True)
         assert np.array_equal(nnb_g[q], nnb_o) and np.array_equal(nz_g[q], nz_o)
         H.assert_fp32_forces(f_g[:, q], f_o, scale)
+
+
+def test_blobs_100k_positions_after_10_iterations_fp32():
+    # a standalone 100k-agent run at the 10M workload's density: FP32 form
+    # against the FP64 oracle, positions after 10 iterations (re-sort at 0)
+    w = H.small_blobs(n=100_000, seed=3)
+    s = H.gpu_sim(w, precision="fp32")
+    o = H.oracle_state(w)
+    s.step(10)
+    o.step(H.oracle_params(w), 10)
+    pos, a = H.gpu_positions(s)
+    assert np.array_equal(a["uid"], o.uid[: o.n])
+    err = np.abs(pos - o.positions()).max()
+    assert err <= 1e-4, err
 
 
 def test_ensemble_512_members_match_independent_runs_fp32():
