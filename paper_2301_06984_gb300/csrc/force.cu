@@ -184,6 +184,26 @@ __device__ __forceinline__ int pair_f64(const DevParams &P, const dbl4 &q, const
                                         double &fz) {
   return pair_f64_k(P.R2, P.k, P.gamma, q, c, fx, fy, fz);
 }
+// The same pair as pair_f64, returning the three products sc * (q - c) that
+// pair_f64 adds to the running sum (so a caller can add them later, in the
+// same order, with the same IEEE operations).
+__device__ __forceinline__ int pair_f64_terms(const DevParams &P, const dbl4 &q, const dbl4 &c, double &tx, double &ty,
+                                              double &tz) {
+  const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
+  const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
+  if (!(d2 < P.R2)) return 0;
+  if (d2 == 0.0) return 1;
+  const double d = __dsqrt_rn(d2);
+  const double delta = __dsub_rn(__dadd_rn(q.w, c.w), d);
+  if (!(delta > 0.0)) return 1;
+  const double rbar = __ddiv_rn(__dmul_rn(q.w, c.w), __dadd_rn(q.w, c.w));
+  const double F = __dsub_rn(__dmul_rn(P.k, delta), __dmul_rn(P.gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
+  const double sc = __ddiv_rn(F, d);
+  tx = __dmul_rn(sc, ddx);
+  ty = __dmul_rn(sc, ddy);
+  tz = __dmul_rn(sc, ddz);
+  return 2;
+}
 
 __device__ __forceinline__ bool is_nbr_f64(const DevParams &P, const dbl4 &q, const dbl4 &c) {
   const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
@@ -623,6 +643,62 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 if (pass == 0) c_cand += (fill > (unsigned)sub) ? (fill - sub + S - 1) / S : 0u;
               }
               // ---- evaluate the queued pairs
+              if (PREC == 0 && (MODE == FM_STEP || MODE == FM_FORCES)) {
+                // FP64 form: the warp evaluates the pooled queues of its lanes
+                // 32 pairs at a time (every lane busy on the slow FP64 pipe),
+                // writing each pair's terms to shared memory (aliasing the
+                // staged FP32 records, which the FP64 pairs do not read); each
+                // owner lane then adds its own pairs' terms in its queue order,
+                // the canonical order, with the same IEEE operations as one
+                // lane evaluating its queue.
+                unsigned inc = qlen;
+                for (int of = 1; of < 32; of <<= 1) {
+                  const unsigned y = __shfl_up_sync(0xffffffffu, inc, of);
+                  if (lane >= of) inc += y;
+                }
+                const unsigned tot = __shfl_sync(0xffffffffu, inc, 31), mine = inc - qlen;
+                double *const tr = (double *)sc;               // [3][32] terms of a tile
+                int *const rr = (int *)(tr + 96);              // [32] pair results
+                uint32_t *const qs = (uint32_t *)(rr + 32);    // [32] pooled queue starts
+                uint32_t *const kqs = qs + 32;                 // [32] the lanes' agents
+                __syncwarp();
+                qs[lane] = mine;
+                kqs[lane] = kq;
+                __syncwarp();
+                for (unsigned t0 = 0; t0 < tot; t0 += 32) {
+                  const unsigned e = t0 + (unsigned)lane;
+                  double tx = 0.0, ty = 0.0, tz = 0.0;
+                  int r = 0;
+                  if (e < tot) {
+                    int ow = 0;  // the lane whose queue holds pooled entry e
+                    for (int st = 16; st > 0; st >>= 1)
+                      if (ow + st < 32 && qs[ow + st] <= e) ow += st;
+                    const unsigned kj = skj[s_q[warp][e - qs[ow]][ow]];
+                    const unsigned ko = kqs[ow];
+                    if (kj != ko) r = pair_f64_terms(P, B.c64[ko], B.c64[kj], tx, ty, tz);
+                  }
+                  __syncwarp();
+                  tr[lane] = tx;
+                  tr[32 + lane] = ty;
+                  tr[64 + lane] = tz;
+                  rr[lane] = r;
+                  __syncwarp();
+                  const unsigned lo = max(mine, t0), hi = min(mine + qlen, t0 + 32u);
+                  for (unsigned u = lo; u < hi; ++u) {
+                    const unsigned t = u - t0;
+                    const int ru = rr[t];
+                    nnb += (ru > 0);
+                    if (ru == 2) {
+                      ncont++;
+                      dfx = __dadd_rn(dfx, tr[t]);
+                      dfy = __dadd_rn(dfy, tr[32 + t]);
+                      dfz = __dadd_rn(dfz, tr[64 + t]);
+                    }
+                  }
+                  __syncwarp();
+                }
+                continue;
+              }
               const unsigned mx = __reduce_max_sync(0xffffffffu, qlen);
               for (unsigned m = 0; m < mx; ++m) {
                 if (m >= qlen) continue;
