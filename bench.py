@@ -264,6 +264,10 @@ def run_other(args):
             tuning = sim.autotune(trial_steps=3)
         sim.step(args.warmup)
         ms = timed_steps(sim, args.steps, stream)
+        sim.profile_begin()
+        sim.step(1)
+        phases = sim.profile_end()
+        line["phases_ms_per_step"] = {k: round(v[0], 4) for k, v in phases.items()}
         line.update(value=w.n * args.steps / (ms * 1e-3), ms_per_step=ms / args.steps, dtype="f32",
                     config={"workload": "ensemble-512: 512 independent simulations, 10^U[3,5] agents each, "
                                         "0.25 volume fraction cubes, d = 10 um, dt U[0.005,0.02]; all "
