@@ -50,7 +50,7 @@ extern "C" {
 #define BDM_ENOMEM (-2)    /* device or host allocation failed                             */
 #define BDM_ECUDA (-3)     /* a CUDA call failed (message holds the CUDA error string)     */
 #define BDM_ECAPACITY (-4) /* agents (with daughters) would exceed `capacity`              */
-#define BDM_ETIMEOUT (-5)  /* a bounded device-side wait gave up                           */
+#define BDM_ETIMEOUT (-5)  /* reserved: no kernel of this library waits, so none returns it  */
 #define BDM_ESTATE (-6)    /* call out of order (e.g. bdm_step before bdm_set_agents)       */
 
 /* precision forms */
