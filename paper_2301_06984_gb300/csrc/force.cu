@@ -291,6 +291,22 @@ __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParam
 // maximum displacement, random walk added after the clamp), grows and divides
 // (FP64 form), writes the new position when it or the previous one moved,
 // and records the flags and the simulation's bounding box.
+// FP32 form of the displacement before the random walk (Sec. 5): dt F when
+// |F| exceeds the adherence, scaled down to the maximum displacement.
+__device__ __forceinline__ void displacement_f32(const DevParams &P, float dt_f, float fx, float fy, float fz,
+                                                 float &ux, float &uy, float &uz) {
+  ux = uy = uz = 0.f;
+  const float fn2 = fmaf(fx, fx, fmaf(fy, fy, fz * fz));
+  if (fn2 > P.adherencef * P.adherencef) {
+    ux = dt_f * fx; uy = dt_f * fy; uz = dt_f * fz;
+    const float dn2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+    if (dn2 > P.dmaxf * P.dmaxf) {
+      const float c = P.dmaxf * rsqrtf(dn2);
+      ux *= c; uy *= c; uz *= c;
+    }
+  }
+}
+
 template <int PREC, int MODE>
 __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, int nxt,
                                              long long step, double dt, float dt_f, uint32_t iq, uint8_t fl,
@@ -318,16 +334,8 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
   } else {
     const uint8_t beh = (P.walk || P.grow) ? A.beh[iq] : (uint8_t)0;
     if (PREC == 1) {
-      float ux = 0.f, uy = 0.f, uz = 0.f;
-      const float fn2 = fmaf(ffx, ffx, fmaf(ffy, ffy, ffz * ffz));
-      if (fn2 > P.adherencef * P.adherencef) {
-        ux = dt_f * ffx; uy = dt_f * ffy; uz = dt_f * ffz;
-        const float dn2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
-        if (dn2 > P.dmaxf * P.dmaxf) {
-          const float c = P.dmaxf * rsqrtf(dn2);
-          ux *= c; uy *= c; uz *= c;
-        }
-      }
+      float ux, uy, uz;
+      displacement_f32(P, dt_f, ffx, ffy, ffz, ux, uy, uz);
       if (P.walk && (beh & BEH_WALK)) {
         float u[3];
         unit_vector_f32(P.seed, A.uid[iq], (uint64_t)step, PURPOSE_WALK, u);
@@ -409,6 +417,50 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
   atomicMin(&bb_w[2], enc_f64(nzp));
   atomicMax(&bb_w[5], enc_f64(nzp));
 }
+// x and y components of a - b in one packed FP32 subtraction (sub.f32x2,
+// sm_100 and later): each half is rounded like a scalar subtraction, so the
+// result is bit-identical to two scalar ones at half the issue slots.
+__device__ __forceinline__ float2 sub_xy(const float4 &a, const float4 &b) {
+  float2 r;
+  asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n"
+      " sub.rn.f32x2 rd, ra, rb;\n mov.b64 {%0, %1}, rd;\n}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+
+// FP32 squared distance of the prefilter, fma(ex, ex, fma(ey, ey, ez ez)).
+__device__ __forceinline__ float dist2_f32(const float4 &q, const float4 &c) {
+  const float2 e = sub_xy(q, c);
+  const float ez = q.z - c.z;
+  return fmaf(e.x, e.x, fmaf(e.y, e.y, ez * ez));
+}
+
+// One lane's share of a staged chunk: candidates sub, sub + S, sub + 2S, ...
+// below fill, each queued (its chunk position, one byte per slot, slots 32
+// bytes apart) when its FP32 squared distance is below R2.  SS > 0 fixes the
+// stride at compile time.  Returns the number of queued candidates; the queue
+// keeps the candidates' order.
+template <int SS>
+__device__ __forceinline__ unsigned scan_chunk(const float4 *sc, uint8_t *q, const float4 cq, unsigned sub,
+                                               unsigned S_, unsigned fill, float R2) {
+  const unsigned S = SS > 0 ? (unsigned)SS : S_;
+  uint8_t *const q0 = q;
+  unsigned i = sub;
+  // four independent candidates per iteration (latency hiding)
+  for (; i + 3u * S < fill; i += 4u * S) {
+    const float e0 = dist2_f32(cq, sc[i]), e1 = dist2_f32(cq, sc[i + S]);
+    const float e2 = dist2_f32(cq, sc[i + 2 * S]), e3 = dist2_f32(cq, sc[i + 3 * S]);
+    if (e0 < R2) { *q = (uint8_t)i; q += 32; }
+    if (e1 < R2) { *q = (uint8_t)(i + S); q += 32; }
+    if (e2 < R2) { *q = (uint8_t)(i + 2 * S); q += 32; }
+    if (e3 < R2) { *q = (uint8_t)(i + 3 * S); q += 32; }
+  }
+  for (; i < fill; i += S)
+    if (dist2_f32(cq, sc[i]) < R2) { *q = (uint8_t)i; q += 32; }
+  return (unsigned)(q - q0) >> 5;
+}
+
 template <int PREC, int MODE>
 __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevParams P) {
   __shared__ int s_nocc[27];
@@ -617,29 +669,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
               // ---- test the chunk in FP32, queue the candidates inside the band
               unsigned qlen = 0;
               if (act) {
-                // four independent candidates per iteration (latency hiding)
-                unsigned i = sub;
-                for (; i + 3u * S < fill; i += 4u * S) {
-                  const float4 c0 = sc[i], c1 = sc[i + S], c2 = sc[i + 2 * S], c3 = sc[i + 3 * S];
-                  float ex = cq.x - c0.x, ey = cq.y - c0.y, ez = cq.z - c0.z;
-                  const float e0 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  ex = cq.x - c1.x; ey = cq.y - c1.y; ez = cq.z - c1.z;
-                  const float e1 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  ex = cq.x - c2.x; ey = cq.y - c2.y; ez = cq.z - c2.z;
-                  const float e2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  ex = cq.x - c3.x; ey = cq.y - c3.y; ez = cq.z - c3.z;
-                  const float e3 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  if (e0 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)i;
-                  if (e1 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + S);
-                  if (e2 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + 2 * S);
-                  if (e3 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)(i + 3 * S);
-                }
-                for (; i < fill; i += S) {
-                  const float4 c = sc[i];
-                  const float ex = cq.x - c.x, ey = cq.y - c.y, ez = cq.z - c.z;
-                  const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  if (d2 < P.R2_hi_f) s_q[warp][qlen++][lane] = (uint8_t)i;
-                }
+                // the default stride (4 lanes per agent) with constant offsets
+                qlen = (S == 4) ? scan_chunk<4>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, 4u, fill, P.R2_hi_f)
+                                : scan_chunk<0>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, (unsigned)S, fill,
+                                                P.R2_hi_f);
                 if (pass == 0) c_cand += (fill > (unsigned)sub) ? (fill - sub + S - 1) / S : 0u;
               }
               // ---- evaluate the queued pairs
@@ -823,6 +856,39 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           ffx += gfx;
           ffy += gfy;
           ffz += gfz;
+        }
+        if (PREC == 1 && MODE == FM_STEP && S >= 4 && !P.walk && !P.grow) {
+          // Lanes 0, 1 and 2 of the agent finish one axis each (one FP64
+          // position load, addition, store and bounding-box update per lane),
+          // with the same arithmetic as finish_agent's FP32 form.
+          float ux, uy, uz;
+          displacement_f32(P, dt_f, ffx, ffy, ffz, ux, uy, uz);
+          const bool live = valid && !is_static && sub < 3;
+          double p = 0.0, np = 0.0;
+          if (live) {
+            p = ((sub == 0) ? A.x[cur] : (sub == 1) ? A.y[cur] : A.z[cur])[iq];
+            const float u = (sub == 0) ? ux : (sub == 1) ? uy : uz;
+            np = (u != 0.f) ? __dadd_rn(p, ftod_exact(u)) : p;
+          }
+          const unsigned mv = __ballot_sync(0xffffffffu, live && np != p);
+          const bool moved = ((mv >> (lane - sub)) & 7u) != 0u;
+          if (live) {
+            if ((fl & FL_MOVED) || moved) ((sub == 0) ? A.x[nxt] : (sub == 1) ? A.y[nxt] : A.z[nxt])[iq] = np;
+            if (P.keep_forces) B.fdbg[(size_t)sub * B.cap + iq] = ftod_exact((sub == 0) ? ffx : (sub == 1) ? ffy : ffz);
+            atomicMin(&s_bb[warp][sub], enc_f64(np));
+            atomicMax(&s_bb[warp][3 + sub], enc_f64(np));
+            if (sub == 0) {
+              c_nbr += nnb;
+              c_cont += ncont;
+              c_moved += moved;
+              A.nz[iq] = (uint16_t)min(ncont, 65535u);
+              A.flags[iq] = moved ? (uint8_t)(FL_MOVED | FL_CHANGED) : (uint8_t)0;
+            }
+          } else if (valid && sub == 0) {
+            c_nbr += nnb;
+            c_cont += ncont;
+          }
+          continue;
         }
         if (!valid || sub != 0) continue;
         c_nbr += nnb;
