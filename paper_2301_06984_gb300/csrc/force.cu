@@ -461,8 +461,12 @@ __device__ __forceinline__ unsigned scan_chunk(const float4 *sc, uint8_t *q, con
   return (unsigned)(q - q0) >> 5;
 }
 
-template <int PREC, int MODE>
+// SPLIT (FP32 step without random walk or growth only): the agent's lanes
+// finish one axis each.  A separate instantiation, so that the other forms
+// keep the register allocation they have without that code.
+template <int PREC, int MODE, bool SPLIT = false>
 __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevParams P) {
+  static_assert(!SPLIT || (PREC == 1 && MODE == FM_STEP), "the split epilogue is the FP32 step's");
   __shared__ int s_nocc[27];
   __shared__ unsigned long long s_ndirty[27];
   __shared__ int s_next;
@@ -470,6 +474,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ uint8_t s_order[64];
   __shared__ unsigned long long s_need;
   __shared__ long long s_o;
+  __shared__ double s_pos[FORCE_WARPS][32];  // SPLIT: each lane's position, copied ahead
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[FORCE_WARPS][6];
   // per warp: a staged chunk of candidate records (box offset applied) and
@@ -607,6 +612,14 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         if (PREC == 0) dq = B.c64[kq];
         const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
         const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+        if (SPLIT && S >= 4 && valid && !is_static && sub < 3) {
+          // this lane's axis of the agent's position, copied to shared memory
+          // while the pairs are evaluated (waited for in the epilogue)
+          const double *const gp = ((sub == 0) ? A.x[cur] : (sub == 1) ? A.y[cur] : A.z[cur]) + iq;
+          const unsigned sa = (unsigned)__cvta_generic_to_shared(&s_pos[warp][lane]);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gp) : "memory");
+          asm volatile("cp.async.commit_group;\n" ::: "memory");
+        }
         const bool compute = valid && !is_static;
         float ffx = 0.f, ffy = 0.f, ffz = 0.f;
         float gfx = 0.f, gfy = 0.f, gfz = 0.f, gbound = 0.f, fscale = 0.f;
@@ -857,16 +870,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           ffy += gfy;
           ffz += gfz;
         }
-        if (PREC == 1 && MODE == FM_STEP && S >= 4 && !P.walk && !P.grow) {
+        if (SPLIT && S >= 4) {
           // Lanes 0, 1 and 2 of the agent finish one axis each (one FP64
-          // position load, addition, store and bounding-box update per lane),
+          // position addition, store and bounding-box update per lane),
           // with the same arithmetic as finish_agent's FP32 form.
           float ux, uy, uz;
           displacement_f32(P, dt_f, ffx, ffy, ffz, ux, uy, uz);
           const bool live = valid && !is_static && sub < 3;
           double p = 0.0, np = 0.0;
           if (live) {
-            p = ((sub == 0) ? A.x[cur] : (sub == 1) ? A.y[cur] : A.z[cur])[iq];
+            asm volatile("cp.async.wait_all;\n" ::: "memory");
+            p = s_pos[warp][lane];
             const float u = (sub == 0) ? ux : (sub == 1) ? uy : uz;
             np = (u != 0.f) ? __dadd_rn(p, ftod_exact(u)) : p;
           }
@@ -1683,7 +1697,10 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
     }
   } else {
     switch (mode) {
-      case FM_STEP: LF(1, FM_STEP); break;
+      case FM_STEP:
+        if (!P.walk && !P.grow) k_force<1, FM_STEP, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, P);
+        else LF(1, FM_STEP);
+        break;
       case FM_FORCES: LF(1, FM_FORCES); break;
       case FM_COUNT_NBR: LF(1, FM_COUNT_NBR); break;
       default: LF(1, FM_LIST_NBR); break;
