@@ -474,6 +474,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ uint8_t s_order[64];
   __shared__ unsigned long long s_need;
   __shared__ long long s_o;
+  // per-warp statistics in shared memory rather than registers (fewer spills):
+  // candidates, neighbours, contacts, FP64 decisions
+  __shared__ unsigned long long s_ctr[FORCE_WARPS][4];
   __shared__ double s_pos[FORCE_WARPS][32];  // SPLIT: each lane's position, copied ahead
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[FORCE_WARPS][6];
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   const long long n_occ = C->n_occ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long step = C->step;
-  unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
+  unsigned c_static = 0, c_moved = 0;
   int wsim = -1;
   int fetch_phase = 0;
   if (threadIdx.x < 27) {
@@ -500,6 +503,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
     s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
   }
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
+  if (lane < 4) s_ctr[warp][lane] = 0ull;
 
   // One block per occupied brick (taken from a global counter); its warps
   // take the brick's 64 boxes from a block counter.
@@ -621,6 +625,11 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           asm volatile("cp.async.commit_group;\n" ::: "memory");
         }
         const bool compute = valid && !is_static;
+        {
+          // candidates tested in pass 0: the whole stencil for each computing agent
+          const unsigned na = __popc(__ballot_sync(0xffffffffu, compute));
+          if (lane == 0) s_ctr[warp][0] += (unsigned long long)ctot * (na / (unsigned)S);
+        }
         float ffx = 0.f, ffy = 0.f, ffz = 0.f;
         float gfx = 0.f, gfy = 0.f, gfz = 0.f, gbound = 0.f, fscale = 0.f;
         double dfx = 0.0, dfy = 0.0, dfz = 0.0;
@@ -686,7 +695,6 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 qlen = (S == 4) ? scan_chunk<4>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, 4u, fill, P.R2_hi_f)
                                 : scan_chunk<0>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, (unsigned)S, fill,
                                                 P.R2_hi_f);
-                if (pass == 0) c_cand += (fill > (unsigned)sub) ? (fill - sub + S - 1) / S : 0u;
               }
               // ---- evaluate the queued pairs
               if (PREC == 0 && (MODE == FM_STEP || MODE == FM_FORCES)) {
@@ -772,7 +780,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
                   bool isn = true;
                   if (band && d2 > P.R2_lo_f) {
-                    c_exact++;
+                    atomicAdd(&s_ctr[warp][3], 1ull);
                     isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
                   }
                   if (isn) {
@@ -786,7 +794,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 if (pass == 1 && (band || d2 > s2 - W)) continue;  // not an FP32 contact
                 if (band || (d2 > s2 - W && d2 < s2 + W)) {
                   // cutoff or contact decided in FP64
-                  c_exact++;
+                  atomicAdd(&s_ctr[warp][3], 1ull);
                   double gx = 0.0, gy = 0.0, gz = 0.0;
                   const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
                   nnb += (r > 0);
@@ -810,7 +818,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   // refinement: the grazing contacts of pass 0, classified by the
                   // same FP32 arithmetic, redone in FP64
                   if (delta < P.graze) {
-                    c_exact++;
+                    atomicAdd(&s_ctr[warp][3], 1ull);
                     pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
                   }
                   continue;
@@ -892,21 +900,24 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
             atomicMin(&s_bb[warp][sub], enc_f64(np));
             atomicMax(&s_bb[warp][3 + sub], enc_f64(np));
             if (sub == 0) {
-              c_nbr += nnb;
-              c_cont += ncont;
               c_moved += moved;
               A.nz[iq] = (uint16_t)min(ncont, 65535u);
               A.flags[iq] = moved ? (uint8_t)(FL_MOVED | FL_CHANGED) : (uint8_t)0;
             }
-          } else if (valid && sub == 0) {
-            c_nbr += nnb;
-            c_cont += ncont;
+          }
+          {
+            const unsigned gn = __reduce_add_sync(0xffffffffu, (valid && sub == 0) ? nnb : 0u);
+            const unsigned gc = __reduce_add_sync(0xffffffffu, (valid && sub == 0) ? ncont : 0u);
+            if (lane == 0) {
+              atomicAdd(&s_ctr[warp][1], (unsigned long long)gn);
+              atomicAdd(&s_ctr[warp][2], (unsigned long long)gc);
+            }
           }
           continue;
         }
         if (!valid || sub != 0) continue;
-        c_nbr += nnb;
-        c_cont += ncont;
+        atomicAdd(&s_ctr[warp][1], (unsigned long long)nnb);
+        atomicAdd(&s_ctr[warp][2], (unsigned long long)ncont);
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
         if (is_static) continue;  // finished by the static pass
@@ -918,8 +929,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
     }
   }
   if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
-  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = wsum64(c_cand),
-                           t_nbr = wsum64(c_nbr), t_cont = wsum64(c_cont), t_exact = wsum64(c_exact);
+  __syncwarp();
+  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = s_ctr[warp][0],
+                           t_nbr = s_ctr[warp][1], t_cont = s_ctr[warp][2], t_exact = s_ctr[warp][3];
   if (lane == 0) {
     if (t_static) atomicAdd(&C->a_static, t_static);
     if (t_moved) atomicAdd(&C->a_moved, t_moved);
