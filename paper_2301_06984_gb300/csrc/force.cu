@@ -475,8 +475,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ unsigned long long s_need;
   __shared__ long long s_o;
   // per-warp statistics in shared memory rather than registers (fewer spills):
-  // candidates, neighbours, contacts, FP64 decisions
-  __shared__ unsigned long long s_ctr[FORCE_WARPS][4];
+  // candidates, neighbours, contacts, FP64 decisions (32-bit shared atomics)
+  __shared__ unsigned s_ctr[FORCE_WARPS][4];
   __shared__ double s_pos[FORCE_WARPS][32];  // SPLIT: each lane's position, copied ahead
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[FORCE_WARPS][6];
@@ -503,7 +503,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
     s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
   }
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
-  if (lane < 4) s_ctr[warp][lane] = 0ull;
+  if (lane < 4) s_ctr[warp][lane] = 0u;
 
   // One block per occupied brick (taken from a global counter); its warps
   // take the brick's 64 boxes from a block counter.
@@ -628,7 +628,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         {
           // candidates tested in pass 0: the whole stencil for each computing agent
           const unsigned na = __popc(__ballot_sync(0xffffffffu, compute));
-          if (lane == 0) s_ctr[warp][0] += (unsigned long long)ctot * (na / (unsigned)S);
+          if (lane == 0) s_ctr[warp][0] += ctot * (na / (unsigned)S);
         }
         float ffx = 0.f, ffy = 0.f, ffz = 0.f;
         float gfx = 0.f, gfy = 0.f, gfz = 0.f, gbound = 0.f, fscale = 0.f;
@@ -780,7 +780,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
                   bool isn = true;
                   if (band && d2 > P.R2_lo_f) {
-                    atomicAdd(&s_ctr[warp][3], 1ull);
+                    atomicAdd(&s_ctr[warp][3], 1u);
                     isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
                   }
                   if (isn) {
@@ -794,7 +794,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 if (pass == 1 && (band || d2 > s2 - W)) continue;  // not an FP32 contact
                 if (band || (d2 > s2 - W && d2 < s2 + W)) {
                   // cutoff or contact decided in FP64
-                  atomicAdd(&s_ctr[warp][3], 1ull);
+                  atomicAdd(&s_ctr[warp][3], 1u);
                   double gx = 0.0, gy = 0.0, gz = 0.0;
                   const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
                   nnb += (r > 0);
@@ -818,7 +818,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   // refinement: the grazing contacts of pass 0, classified by the
                   // same FP32 arithmetic, redone in FP64
                   if (delta < P.graze) {
-                    atomicAdd(&s_ctr[warp][3], 1ull);
+                    atomicAdd(&s_ctr[warp][3], 1u);
                     pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
                   }
                   continue;
@@ -908,16 +908,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           {
             const unsigned gn = __reduce_add_sync(0xffffffffu, (valid && sub == 0) ? nnb : 0u);
             const unsigned gc = __reduce_add_sync(0xffffffffu, (valid && sub == 0) ? ncont : 0u);
-            if (lane == 0) {
-              atomicAdd(&s_ctr[warp][1], (unsigned long long)gn);
-              atomicAdd(&s_ctr[warp][2], (unsigned long long)gc);
-            }
+            if (lane == 0) { atomicAdd(&s_ctr[warp][1], gn); atomicAdd(&s_ctr[warp][2], gc); }
           }
           continue;
         }
         if (!valid || sub != 0) continue;
-        atomicAdd(&s_ctr[warp][1], (unsigned long long)nnb);
-        atomicAdd(&s_ctr[warp][2], (unsigned long long)ncont);
+        atomicAdd(&s_ctr[warp][1], nnb);
+        atomicAdd(&s_ctr[warp][2], ncont);
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
         if (is_static) continue;  // finished by the static pass
