@@ -284,13 +284,6 @@ __device__ __forceinline__ void flush_bbox_warp(const DevBufs &B, const DevParam
   __syncwarp();
 }
 
-// Per-agent end of the force kernels (px, py, pz: the agent's position P_t).
-// FM_FORCES records the summed force and the contact and neighbour counts in
-// the debug buffers.  FM_STEP forms
-// the displacement (Sec. 5: dt F unless |F| <= adherence, clamped to the
-// maximum displacement, random walk added after the clamp), grows and divides
-// (FP64 form), writes the new position when it or the previous one moved,
-// and records the flags and the simulation's bounding box.
 // FP32 form of the displacement before the random walk (Sec. 5): dt F when
 // |F| exceeds the adherence, scaled down to the maximum displacement.
 __device__ __forceinline__ void displacement_f32(const DevParams &P, float dt_f, float fx, float fy, float fz,
@@ -307,6 +300,13 @@ __device__ __forceinline__ void displacement_f32(const DevParams &P, float dt_f,
   }
 }
 
+// Per-agent end of the force kernels (px, py, pz: the agent's position P_t).
+// FM_FORCES records the summed force and the contact and neighbour counts in
+// the debug buffers.  FM_STEP forms the displacement
+// (Sec. 5: dt F unless |F| <= adherence, clamped to the
+// maximum displacement, random walk added after the clamp), grows and divides
+// (FP64 form), writes the new position when it or the previous one moved,
+// and records the flags and the simulation's bounding box.
 template <int PREC, int MODE>
 __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, int nxt,
                                              long long step, double dt, float dt_f, uint32_t iq, uint8_t fl,
