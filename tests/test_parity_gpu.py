@@ -381,6 +381,31 @@ def test_fp32_force_kernels_agree_with_oracle(lanes):
     assert occ.max() > 32
 
 
+@pytest.mark.parametrize("walk", [0.0, 0.5])
+@pytest.mark.parametrize("lanes", [0, -1, 1, 2, 4, 8, 32])
+def test_fp32_step_positions_every_force_kernel(lanes, walk):
+    # positions after 3 FP32 iterations against the FP64 oracle for every FP32
+    # force kernel.  Without random walk or growth the step runs the per-axis
+    # epilogue instantiation (lanes 0-2 of an agent finish one axis each; with
+    # the cost model, boxes of fewer than 4 lanes per agent keep the one-lane
+    # epilogue); with the walk it runs the shared instantiation.
+    w = H.small_blobs(n=20_000, seed=23)
+    if walk:
+        w.params["walk_step"] = walk
+        w.beh = np.where(np.arange(w.n) % 2 == 0, W.WALK, 0).astype(np.uint8)
+    s = H.gpu_sim(w, precision="fp32")
+    s.set_force_kernel(lanes)
+    o = H.oracle_state(w)
+    s.step(3)
+    o.step(H.oracle_params(w), 3)
+    pos, a = H.gpu_positions(s)
+    assert np.array_equal(a["uid"], o.uid[: o.n])
+    err = np.abs(pos - o.positions()).max()
+    assert err <= 1e-4, err
+    moved = np.abs(pos - np.stack([w.x, w.y, w.z])).max()
+    assert moved > 1e-3  # the agents did move
+
+
 def test_autotune_fp32_lanes_keep_tolerance():
     w = H.small_blobs(n=40_000, seed=13)
     s = H.gpu_sim(w)
