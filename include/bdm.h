@@ -110,7 +110,12 @@ typedef struct {
   int32_t error;              /* sticky device error word (0 = none)               */
 } bdm_counters;
 
-/* Create a simulation.  `stream` is a cudaStream_t (NULL = legacy default
+/* Create a simulation: the parameters of the paper's problem statement
+ * (Sec. 3.1: interaction radius R and box edge L >= R of the uniform grid;
+ * Sec. 5: the mechanical force, the time step, the static-agent switch
+ * detect_static and the force threshold "adherence"; Sec. 4.2: the agent
+ * sorting frequency sort_every; Sec. 3.2: the capacity that additions by
+ * division may fill).  `stream` is a cudaStream_t (NULL = legacy default
  * stream); all work of this simulation is ordered on it.  On success *out
  * owns device memory for params->capacity agents.
  * Errors: BDM_EINVAL (R <= 0, L < R, n_sims < 1, capacity < 1, precision
@@ -133,8 +138,13 @@ int bdm_set_agents(bdm_sim *sim, int64_t n, const double *xyz, const double *dia
                    const uint64_t *uid, const uint8_t *behavior, const int64_t *sim_offsets, int64_t step,
                    uint64_t next_uid, int mem);
 
-/* Advance n_steps iterations (the per-iteration work is one captured CUDA
- * graph replayed on the simulation's stream).  Blocks until the iterations
+/* Advance n_steps iterations of the simulation loop (Algorithm 1 with the
+ * mechanical operation as its only agent operation: the six steps listed at
+ * the top of this header, i.e. Sec. 4.2 sorting when due, the Sec. 3.1 grid
+ * build, Sec. 5 static detection, force and displacement, behaviours, and
+ * the Sec. 3.2 commit of additions at the end of the iteration).  The
+ * per-iteration work is one captured CUDA graph replayed on the simulation's
+ * stream.  Blocks until the iterations
  * are done and the device counters are read back.  Errors: BDM_ESTATE (no
  * agents set), BDM_EINVAL (n_steps < 0), BDM_ECAPACITY (daughters would
  * exceed capacity; the state is that of the last completed iteration),
@@ -146,7 +156,11 @@ int bdm_step(bdm_sim *sim, int n_steps);
  * does.  Errors: BDM_ESTATE, BDM_ECUDA. */
 int bdm_sort(bdm_sim *sim);
 
-/* Copy the state out (storage order).  Any output pointer may be NULL.  cap
+/* Copy the state out (storage order): the agent attributes the resource
+ * manager holds (Sec. 3.2; after sort steps, storage is in the Morton order
+ * of Sec. 4.2), with the iteration and uid counters needed to resume (the
+ * paper has no checkpoint call; this is its model state).  Any output
+ * pointer may be NULL.  cap
  * is the number of agents the arrays hold (xyz holds 3 x cap, x at 0, y at
  * cap, z at 2 cap); sim_offsets holds n_sims + 1.  *n_out gets the number of
  * agents.  Errors: BDM_ECAPACITY (cap < n; nothing written but *n_out),
@@ -158,8 +172,12 @@ int bdm_get_agents(bdm_sim *sim, int64_t cap, double *xyz, double *diam, double 
 /* Counters of the last iteration (host struct).  Errors: BDM_EINVAL, BDM_ECUDA. */
 int bdm_get_counters(bdm_sim *sim, bdm_counters *out);
 
-/* Diagnostic outputs (host or device memory per `mem` is not offered: `out` is
- * always host memory).  `what`:
+/* Diagnostic outputs: the intermediate results of one iteration that the
+ * paper defines -- the summed force and contact count of the mechanical
+ * operation (Sec. 5), the static flags (Sec. 5, conditions i-iv), the uniform
+ * grid's boxes, geometry and agent order (Sec. 3.1), the Morton ranks of the
+ * gap/offset mapping (Sec. 4.2) and the neighbour sets of the 27-box search
+ * (Sec. 3.1).  `out` is always host memory.  `what`:
  *   BDM_DBG_FORCES       double 3 x n: summed force of the last iteration
  *                        (needs keep_forces; 0 for static agents)
  *   BDM_DBG_NZ           int32 n: contacts (delta > 0) of the last iteration,
@@ -249,9 +267,10 @@ int bdm_set_stream(bdm_sim *sim, void *stream);
 
 /* Summed force on every agent of one simulation without allocating any
  * memory.  The paper has no counterpart: this entry point serves callers that
- * cannot call cudaMalloc -- code recorded inside a CUDA stream capture that
- * must not allocate, host applications whose own allocator owns all device
- * memory, plug-ins forbidden to allocate.  It runs the same grid build and
+ * cannot call cudaMalloc -- host applications whose own allocator owns all
+ * device memory (an allocation behind its back would break its accounting or
+ * fail against its pool), and plug-ins or embedded solvers that their host
+ * forbids to allocate.  It runs the same grid build and
  * force kernels as BDM_DBG_FORCES_NOW in the FP64 form (no displacement, no
  * static skip) on the caller's device buffers: xyz 3 x n doubles (x, y, z
  * blocks), diam n doubles; outputs forces 3 x n doubles (same layout) and
@@ -263,9 +282,11 @@ int bdm_set_stream(bdm_sim *sim, void *stream);
  * array and it keeps the last call's contents, so calls that may overlap on
  * the GPU (other streams, other host threads, same device) race: serialise
  * them.  The first call on a device looks up the array's device address
- * (once per device, with that device current); make that first call before
- * any stream capture.  Work is ordered on `stream` (a cudaStream_t, NULL =
- * legacy default) and the call waits for it to finish.  Errors: BDM_EINVAL,
+ * (once per device, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture.  A
+ * cudaDeviceReset unloads the array from the device, so do not call this
+ * entry point on a device after resetting it.  Work is ordered on `stream` (a
+ * cudaStream_t, NULL = legacy default) and the call waits for it to finish.  Errors: BDM_EINVAL,
  * BDM_ECAPACITY, BDM_ECUDA; bdm_noalloc_last_error() gives the message. */
 int bdm_forces_noalloc(int64_t n, const double *xyz, const double *diam, double interaction_radius,
                        double box_edge, double k, double gamma, double *forces, int32_t *counts, void *stream);

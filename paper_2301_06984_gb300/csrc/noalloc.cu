@@ -2,13 +2,14 @@
 //
 // bdm_forces_noalloc() evaluates the summed overlap force of every agent of
 // one simulation (FP64 form, the same kernels as bdm_get_debug's
-// BDM_DBG_FORCES_NOW) for callers that cannot call cudaMalloc: code running
-// inside a CUDA stream capture that must not allocate, host applications
-// whose allocator owns all device memory, or plug-ins forbidden to allocate.
-// The caller passes device inputs and outputs; every intermediate (grid
-// tables, sorted records, counters) lives in one file-scope device array of
-// fixed size, which every GPU that loads this library holds until the
-// process exits.
+// BDM_DBG_FORCES_NOW) for callers that cannot call cudaMalloc: host
+// applications whose own allocator owns all device memory (a cudaMalloc
+// behind its back would break its accounting or fail against its pool), and
+// plug-ins or embedded solvers that their host forbids to allocate.  The
+// caller passes device inputs and outputs; every intermediate (grid tables,
+// sorted records, counters) lives in one file-scope device array of fixed
+// size, which every GPU that loads this library holds until the process
+// exits.  The call waits for its work to finish before it returns.
 #include <cstring>
 #include <mutex>
 
@@ -88,6 +89,8 @@ extern "C" int bdm_forces_noalloc(int64_t n, const double *xyz, const double *di
   unsigned char *base = nullptr;
   {
     // once per device, with that device current: the array's device address
+    // (cached for the life of the process; a cudaDeviceReset, which unloads
+    // this module from the device, invalidates it -- see bdm.h)
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     if (!g_scratch_ptr[dev]) {
       cudaError_t e = cudaGetSymbolAddress((void **)&g_scratch_ptr[dev], g_noalloc_scratch);
@@ -176,6 +179,10 @@ extern "C" int bdm_forces_noalloc(int64_t n, const double *xyz, const double *di
   launch_scatter(B, dp, lc, st);
   launch_brick_sort(B, dp, lc, st);
   launch_force(B, dp, lc, FM_FORCES, st);
+  // a launch the runtime rejected (no kernel image, bad configuration) would
+  // otherwise leave the outputs unwritten with the device error word still 0
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return na_fail(BDM_ECUDA, "bdm_forces_noalloc: a kernel launch failed");
   int32_t err = 0;
   e = cudaMemcpyAsync(&err, &B.ctr->error, sizeof(err), cudaMemcpyDeviceToHost, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);

@@ -1,6 +1,6 @@
 """The allocation-free entry point bdm_forces_noalloc, for callers that cannot
-call cudaMalloc (stream-capture regions that must not allocate, hosts whose
-allocator owns device memory, plug-ins forbidden to allocate).  It must give
+call cudaMalloc (host applications whose own allocator owns all device memory,
+plug-ins or embedded solvers that their host forbids to allocate).  It must give
 the same forces and counts as the allocating path (bdm_get_debug's
 BDM_DBG_FORCES_NOW in the FP64 form, compared bit for bit as the FP64 tests
 do) on two calls in a row that share its fixed scratch array.  Collected last
