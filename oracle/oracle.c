@@ -16,6 +16,7 @@
  *   Algorithm 1 (simulation loop)           -> orc_step ordering
  *   Sec. 3.1 (uniform grid, 3x3x3 boxes)     -> grid geometry, box lists
  *   Sec. 3.2 (additions at end of iteration)-> division merge (parent order)
+ *   Sec. 3.2 (removal in five steps)         -> orc_remove (swap from the tail)
  *   Sec. 4.2 (Morton order, gap/offset DFS)  -> orc_morton_offsets, sort step
  *   Sec. 5  (static-agent conditions i-iv)   -> static contract
  *   Sec. 5  defers the pair force to Cortex3D without a formula; the force
@@ -28,7 +29,9 @@
  * Philox against numpy's Philox bit generator, cube root against numpy,
  * static-skip == no-skip trajectories, division invariants.
  * Parity unpinned: the division geometry and the random-walk direction have
- * no printed reference; only their invariants are pinned.
+ * no printed reference; only their invariants are pinned.  Removal is pinned
+ * by hand-worked examples of its five steps and by invariants; which agents
+ * die (a Philox draw per agent and iteration) has no printed reference.
  */
 #include <math.h>
 #include <stdint.h>
@@ -42,6 +45,7 @@
 
 #define BEH_GROW 1u
 #define BEH_WALK 2u
+#define BEH_DIE 4u
 
 typedef struct {
   double R;          /* interaction radius: neighbour iff d^2 < R^2, j != i   */
@@ -57,6 +61,7 @@ typedef struct {
   double ratio_lo, ratio_hi;
   double walk_step;      /* random-walk step length for WALK agents             */
   uint64_t seed;
+  double death_prob;     /* per-iteration probability that a DIE agent is removed */
 } orc_params;
 
 typedef struct {
@@ -76,6 +81,11 @@ typedef struct {
   double *fx, *fy, *fz;
   uint8_t *is_static;
   int64_t n_divided, n_static, n_coincident;
+  /* history: positions (at the start of the previous step) of the agents
+   * removed during it; their boxes are dirty for the static test */
+  double *gx, *gy, *gz;
+  int64_t n_ghost;
+  int64_t n_removed; /* output: agents removed by the last orc_step */
 } orc_state;
 
 /* ------------------------------------------------------------------------ */
@@ -112,6 +122,7 @@ static double u53(uint64_t w) { return (double)(w >> 11) * (1.0 / 90071992547409
 #define PURPOSE_RATIO 0u
 #define PURPOSE_AXIS 1u
 #define PURPOSE_WALK 2u
+#define PURPOSE_DEATH 3u
 
 /* Unit vector by Marsaglia's (1972) disc method: draw x1, x2 uniform in
  * [-1,1) until 0 < s = x1^2 + x2^2 < 1; then
@@ -403,7 +414,8 @@ static void grid_range(const grid_t *G, int64_t key, int64_t *first, int64_t *la
 /* ------------------------------------------------------------------------ */
 typedef struct {
   double fx, fy, fz;
-  double scale; /* sum over contacts of k*delta + gamma*sqrt(rbar*delta) (tolerance base) */
+  double scale;     /* sum over contacts of k*delta + gamma*sqrt(rbar*delta) (term magnitudes) */
+  double scale_abs; /* sum over contacts of |k*delta - gamma*sqrt(rbar*delta)| (pair-force magnitudes) */
   int32_t nz;   /* contacts: neighbours with delta > 0 */
   int32_t nnb;  /* neighbours: d^2 < R^2, j != i */
   int32_t ncoincident;
@@ -419,6 +431,7 @@ static void force_on(const orc_state *st, const orc_params *P, const grid_t *G, 
   double xi = st->x[i], yi = st->y[i], zi = st->z[i], ri = st->diam[i] * 0.5;
   a->fx = a->fy = a->fz = 0.0;
   a->scale = 0.0;
+  a->scale_abs = 0.0;
   a->nz = a->nnb = a->ncoincident = 0;
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
@@ -444,6 +457,7 @@ static void force_on(const orc_state *st, const orc_params *P, const grid_t *G, 
           double F = kd - gs;
           double sc = F / d;
           a->scale += kd + gs;
+          a->scale_abs += fabs(F);
           a->fx = a->fx + sc * ddx;
           a->fy = a->fy + sc * ddy;
           a->fz = a->fz + sc * ddz;
@@ -574,11 +588,12 @@ int64_t orc_neighbors_brute(const orc_state *st, const orc_params *P, int64_t *o
 }
 
 /* Summed pair force on selected agents (all when q == NULL), without the
- * static skip; f is 3 x nq SoA; nz, nnb and scale (sum over contacts of the
- * magnitudes of the two force terms, the base of the FP32 tolerance) are
- * optional. */
+ * static skip; f is 3 x nq SoA.  Optional outputs: nz (contacts), nnb
+ * (neighbours), scale (sum over contacts of the magnitudes of the two force
+ * terms) and scale_abs (sum over contacts of the pair-force magnitude |F_ij|,
+ * the base of the FP32 form's relative force tolerance). */
 int orc_forces(const orc_state *st, const orc_params *P, int64_t nq, const int64_t *q, double *f,
-               int32_t *nz, int32_t *nnb, double *scale) {
+               int32_t *nz, int32_t *nnb, double *scale, double *scale_abs) {
   int rc = check_state(st, P);
   if (rc) return rc;
   grid_t G;
@@ -594,6 +609,7 @@ int orc_forces(const orc_state *st, const orc_params *P, int64_t nq, const int64
     if (nz) nz[m] = a.nz;
     if (nnb) nnb[m] = a.nnb;
     if (scale) scale[m] = a.scale;
+    if (scale_abs) scale_abs[m] = a.scale_abs;
   }
   grid_free(&G);
   return ORC_OK;
@@ -640,6 +656,75 @@ static int apply_sort(orc_state *st, const orc_params *P) {
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Removal (Sec. 3.2): the agent vector has no empty elements, so a removed  */
+/* agent left of the new size leaves a hole that a surviving agent from the */
+/* right of it fills.  The paper's five steps, on one thread, with the       */
+/* removed list in ascending storage index.                                  */
+/* ------------------------------------------------------------------------ */
+static void move_agent(orc_state *st, int64_t from, int64_t to) {
+  st->x[to] = st->x[from]; st->y[to] = st->y[from]; st->z[to] = st->z[from];
+  st->px[to] = st->px[from]; st->py[to] = st->py[from]; st->pz[to] = st->pz[from];
+  st->diam[to] = st->diam[from];
+  if (st->vol) st->vol[to] = st->vol[from];
+  st->uid[to] = st->uid[from];
+  st->beh[to] = st->beh[from];
+  st->changed[to] = st->changed[from];
+  st->nz[to] = st->nz[from];
+  if (st->fx) { st->fx[to] = st->fx[from]; st->fy[to] = st->fy[from]; st->fz[to] = st->fz[from]; }
+  if (st->is_static) st->is_static[to] = st->is_static[from];
+}
+
+/* Remove the agents i < st->n with rm[i] != 0.  Returns the number of agents
+ * moved (at most the number removed), or a negative error. */
+int64_t orc_remove(orc_state *st, const uint8_t *rm) {
+  const int64_t n = st->n;
+  /* step 1: number of removed agents, the new size, two auxiliary arrays of
+   * that length */
+  int64_t removed = 0;
+  for (int64_t i = 0; i < n; ++i) removed += rm[i] ? 1 : 0;
+  const int64_t new_size = n - removed;
+  if (removed == 0) return 0;
+  int64_t *to_right = (int64_t *)malloc(sizeof(int64_t) * (size_t)removed);
+  int64_t *to_left = (int64_t *)malloc(sizeof(int64_t) * (size_t)removed);
+  uint8_t *not_to_left = (uint8_t *)calloc((size_t)removed, 1);
+  if (!to_right || !to_left || !not_to_left) {
+    free(to_right); free(to_left); free(not_to_left);
+    return ORC_ENOMEM;
+  }
+  /* step 2: a removed agent left of the new size is a hole (to_right holds
+   * its index, the others hold "none"); one right of it marks not_to_left at
+   * idx - new_size */
+  const int64_t NONE = -1;
+  int64_t k = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!rm[i]) continue;
+    if (i < new_size) {
+      to_right[k] = i;
+    } else {
+      to_right[k] = NONE;
+      not_to_left[i - new_size] = 1;
+    }
+    ++k;
+  }
+  /* step 3: move the entries that mean a swap to the front: the holes in
+   * to_right, and, with not_to_left read as to_left, each zero entry as
+   * array index + new_size (a survivor right of the new size) */
+  int64_t swaps_right = 0, swaps_left = 0;
+  for (int64_t e = 0; e < removed; ++e)
+    if (to_right[e] != NONE) to_right[swaps_right++] = to_right[e];
+  for (int64_t e = 0; e < removed; ++e)
+    if (!not_to_left[e]) to_left[swaps_left++] = e + new_size;
+  /* step 4: the swaps (the prefix sum of the per-thread swap counts is
+   * trivial with one thread); both lists have one entry per hole */
+  const int64_t swaps = swaps_right < swaps_left ? swaps_right : swaps_left;
+  for (int64_t e = 0; e < swaps; ++e) move_agent(st, to_left[e], to_right[e]);
+  /* step 5: shrink */
+  st->n = new_size;
+  free(to_right); free(to_left); free(not_to_left);
+  return swaps;
+}
+
 static int agent_dt(const orc_state *st, const orc_params *P, int64_t sim, double *dt) {
   *dt = st->dt_sim ? st->dt_sim[sim] : P->dt;
   return 0;
@@ -648,7 +733,9 @@ static int agent_dt(const orc_state *st, const orc_params *P, int64_t sim, doubl
 int orc_step(orc_state *st, const orc_params *P) {
   int rc = check_state(st, P);
   if (rc) return rc;
-  if (st->n_sims > 1 && P->growth > 0.0) return ORC_EINVAL; /* ensembles do not divide */
+  if (st->n_sims > 1 && (P->growth > 0.0 || P->death_prob > 0.0))
+    return ORC_EINVAL; /* ensembles neither divide nor remove */
+  if (!st->gx || !st->gy || !st->gz) return ORC_EINVAL;
   int64_t n = st->n;
   const double pi = 3.141592653589793;
 
@@ -666,7 +753,7 @@ int orc_step(orc_state *st, const orc_params *P) {
   /* 3. static marking: dirty boxes hold the old or the new position of an
    *    agent that changed during the previous step */
   uint8_t *stat = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
-  int64_t *dirty = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * n + 1));
+  int64_t *dirty = (int64_t *)malloc(sizeof(int64_t) * (size_t)(2 * n + st->n_ghost + 1));
   if (!stat || !dirty) { free(stat); free(dirty); grid_free(&G); return ORC_ENOMEM; }
   int64_t ndirty = 0;
   int use_static = P->detect_static && st->history_valid;
@@ -681,6 +768,15 @@ int orc_step(orc_state *st, const orc_params *P) {
       int64_t oz = box_coord_raw(st->pz[j], g->lo[2], P->L);
       if (ox >= 0 && ox < g->nb[0] && oy >= 0 && oy < g->nb[1] && oz >= 0 && oz < g->nb[2])
         dirty[ndirty++] = G.base[s] + box_linear(g, ox, oy, oz);
+    }
+    /* agents removed during the previous step: their last boxes are dirty */
+    for (int64_t k = 0; k < st->n_ghost; ++k) {
+      const sim_grid *g = &G.g[0];
+      int64_t ox = box_coord_raw(st->gx[k], g->lo[0], P->L);
+      int64_t oy = box_coord_raw(st->gy[k], g->lo[1], P->L);
+      int64_t oz = box_coord_raw(st->gz[k], g->lo[2], P->L);
+      if (ox >= 0 && ox < g->nb[0] && oy >= 0 && oy < g->nb[1] && oz >= 0 && oz < g->nb[2])
+        dirty[ndirty++] = G.base[0] + box_linear(g, ox, oy, oz);
     }
     qsort(dirty, (size_t)ndirty, sizeof(int64_t), cmp_i64);
     for (int64_t i = 0; i < n; ++i) {
@@ -751,18 +847,25 @@ int orc_step(orc_state *st, const orc_params *P) {
   free(stat);
   free(dirty);
 
-  /* 5. behaviours: growth and the division decision (on the grown volume) */
+  /* 5. behaviours: death (an agent removed at the end of this step neither
+   *    grows nor divides), growth and the division decision (on the grown
+   *    volume) */
   uint8_t *resized = (uint8_t *)calloc((size_t)(n + 1), 1);
-  if (!resized) { free(nx); free(nnz); free(moved); free(divide); grid_free(&G); return ORC_ENOMEM; }
+  uint8_t *rm = (uint8_t *)calloc((size_t)(st->cap + 1), 1);
+  if (!resized || !rm) { free(nx); free(nnz); free(moved); free(divide); free(resized); free(rm); grid_free(&G); return ORC_ENOMEM; }
+  for (int64_t i = 0; i < n; ++i)
+    if ((st->beh[i] & BEH_DIE) && P->death_prob > 0.0)
+      rm[i] = (uint8_t)(orc_uniform(P->seed, st->uid[i], (uint64_t)st->step, PURPOSE_DEATH) < P->death_prob);
   int64_t ndiv = 0;
   for (int64_t i = 0; i < n; ++i) {
+    if (rm[i]) continue;
     if (!((st->beh[i] & BEH_GROW) && P->growth > 0.0)) continue;
     double v = st->vol[i] + P->growth;
     if (v >= P->divide_volume) { divide[i] = 1; ndiv++; }
     resized[i] = 1;
   }
   if (n + ndiv > st->cap) {
-    free(nx); free(nnz); free(moved); free(divide); free(resized); grid_free(&G);
+    free(nx); free(nnz); free(moved); free(divide); free(resized); free(rm); grid_free(&G);
     return ORC_ECAPACITY;
   }
 
@@ -808,12 +911,29 @@ int orc_step(orc_state *st, const orc_params *P) {
     rank++;
   }
   st->n = n + ndiv;
-  st->sim_off[st->n_sims] = st->n; /* division only in single-simulation runs */
+
+  /* 7. removals, after the additions (Sec. 3.2): the removed agents' boxes of
+   *    this step are remembered for the next step's static test, then the
+   *    vector is compacted by swaps from its tail */
+  st->n_ghost = 0;
+  for (int64_t i = 0; i < n; ++i) {
+    if (!rm[i]) continue;
+    st->gx[st->n_ghost] = st->px[i]; st->gy[st->n_ghost] = st->py[i]; st->gz[st->n_ghost] = st->pz[i];
+    st->n_ghost++;
+  }
+  int64_t moved_by_removal = orc_remove(st, rm);
+  if (moved_by_removal < 0) {
+    free(nx); free(nnz); free(moved); free(divide); free(resized); free(rm); grid_free(&G);
+    return ORC_ENOMEM;
+  }
+  st->n_removed = st->n_ghost;
+
+  st->sim_off[st->n_sims] = st->n; /* division and removal only in single-simulation runs */
   st->next_uid += (uint64_t)ndiv;
   st->n_divided = ndiv;
   st->step += 1;
   st->history_valid = 1;
-  free(nx); free(nnz); free(moved); free(divide); free(resized);
+  free(nx); free(nnz); free(moved); free(divide); free(resized); free(rm);
   grid_free(&G);
   return ORC_OK;
 }

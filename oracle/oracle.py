@@ -51,7 +51,7 @@ class Params(C.Structure):
         ("detect_static", C.c_int32), ("sort_every", C.c_int32),
         ("growth", C.c_double), ("divide_volume", C.c_double),
         ("ratio_lo", C.c_double), ("ratio_hi", C.c_double), ("walk_step", C.c_double),
-        ("seed", C.c_uint64),
+        ("seed", C.c_uint64), ("death_prob", C.c_double),
     ]
 
 
@@ -71,6 +71,8 @@ class _State(C.Structure):
         ("fx", _P(C.c_double)), ("fy", _P(C.c_double)), ("fz", _P(C.c_double)),
         ("is_static", _P(C.c_uint8)),
         ("n_divided", C.c_int64), ("n_static", C.c_int64), ("n_coincident", C.c_int64),
+        ("gx", _P(C.c_double)), ("gy", _P(C.c_double)), ("gz", _P(C.c_double)),
+        ("n_ghost", C.c_int64), ("n_removed", C.c_int64),
     ]
 
 
@@ -88,7 +90,7 @@ def _declare(L):
     L.orc_neighbors.restype = C.c_int64
     L.orc_neighbors_brute.argtypes = [SP, PP, vp, vp, C.c_int64]
     L.orc_neighbors_brute.restype = C.c_int64
-    L.orc_forces.argtypes = [SP, PP, C.c_int64, vp, vp, vp, vp, vp]
+    L.orc_forces.argtypes = [SP, PP, C.c_int64, vp, vp, vp, vp, vp, vp]
     L.orc_forces.restype = C.c_int
     L.orc_philox4x64_10.argtypes = [vp, vp, vp]
     L.orc_philox4x64_10.restype = None
@@ -102,13 +104,15 @@ def _declare(L):
     L.orc_morton3.restype = C.c_uint64
     L.orc_morton2.argtypes = [C.c_uint64, C.c_uint64]
     L.orc_morton2.restype = C.c_uint64
+    L.orc_remove.argtypes = [SP, vp]
+    L.orc_remove.restype = C.c_int64
     L.orc_morton_offsets.argtypes = [C.c_int32, vp, vp, vp, C.c_int64]
     L.orc_morton_offsets.restype = C.c_int64
 
 
 DEFAULTS = dict(R=12.0, L=0.0, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.0,
                 detect_static=0, sort_every=0, growth=0.0, divide_volume=0.0,
-                ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, seed=0)
+                ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, seed=0, death_prob=0.0)
 
 
 def make_params(**kw) -> Params:
@@ -158,12 +162,13 @@ class State:
         self.px, self.py, self.pz = self.x.copy(), self.y.copy(), self.z.copy()
         self.fx, self.fy, self.fz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
         self.is_static = np.zeros(cap, np.uint8)
+        self.gx, self.gy, self.gz = np.zeros(cap), np.zeros(cap), np.zeros(cap)
         self._s = _State()
         s = self._s
         s.n, s.cap, s.n_sims, s.history_valid = n, cap, len(self.sim_off) - 1, 0
         s.step = step
         s.next_uid = n if next_uid is None else next_uid
-        for name in ("x", "y", "z", "diam", "vol", "px", "py", "pz", "fx", "fy", "fz"):
+        for name in ("x", "y", "z", "diam", "vol", "px", "py", "pz", "fx", "fy", "fz", "gx", "gy", "gz"):
             setattr(s, name, getattr(self, name).ctypes.data_as(C.POINTER(C.c_double)))
         s.uid = self.uid.ctypes.data_as(C.POINTER(C.c_uint64))
         s.beh = self.beh.ctypes.data_as(C.POINTER(C.c_uint8))
@@ -190,7 +195,8 @@ class State:
     @property
     def counters(self):
         s = self._s
-        return dict(n_divided=s.n_divided, n_static=s.n_static, n_coincident=s.n_coincident)
+        return dict(n_divided=s.n_divided, n_static=s.n_static, n_coincident=s.n_coincident,
+                    n_removed=s.n_removed)
 
     def positions(self):
         n = self.n
@@ -207,6 +213,17 @@ class State:
             rc = L.orc_step(C.byref(self._s), C.byref(params))
             if rc != 0:
                 raise RuntimeError("orc_step failed: %d" % rc)
+
+    def remove(self, rm):
+        """Remove the agents flagged in rm (length n) by the parallel-removal
+        steps of Sec. 3.2; returns the number of agents moved."""
+        r = np.zeros(max(self.n, 1), np.uint8)
+        r[: self.n] = np.asarray(rm, dtype=np.uint8)[: self.n]
+        m = lib().orc_remove(C.byref(self._s), _ptr(r))
+        if m < 0:
+            raise RuntimeError("orc_remove failed: %d" % m)
+        self.sim_off[-1] = self.n
+        return int(m)
 
     def grid(self, params: Params):
         n = self.n
@@ -246,20 +263,27 @@ class State:
     def neighbors_brute(self, params: Params):
         return self._csr(lib().orc_neighbors_brute, params)
 
-    def forces_of(self, params: Params, q=None, with_scale=False):
+    def forces_of(self, params: Params, q=None, with_scale=False, with_scale_abs=False):
+        """Forces (3 x nq), contacts and neighbours of the agents q (all when
+        None); with_scale adds the sum of the force terms' magnitudes, and
+        with_scale_abs the sum of the pair-force magnitudes, per agent."""
         nq = self.n if q is None else len(q)
         qa = None if q is None else np.ascontiguousarray(q, dtype=np.int64)
         f = np.zeros((3, max(nq, 1)))
         nz = np.zeros(max(nq, 1), np.int32)
         nnb = np.zeros(max(nq, 1), np.int32)
         sc = np.zeros(max(nq, 1))
+        sa = np.zeros(max(nq, 1))
         rc = lib().orc_forces(C.byref(self._s), C.byref(params), nq, _ptr(qa), _ptr(f), _ptr(nz), _ptr(nnb),
-                              _ptr(sc))
+                              _ptr(sc), _ptr(sa))
         if rc != 0:
             raise RuntimeError("orc_forces failed: %d" % rc)
+        out = [f[:, :nq], nz[:nq], nnb[:nq]]
         if with_scale:
-            return f[:, :nq], nz[:nq], nnb[:nq], sc[:nq]
-        return f[:, :nq], nz[:nq], nnb[:nq]
+            out.append(sc[:nq])
+        if with_scale_abs:
+            out.append(sa[:nq])
+        return tuple(out)
 
 
 def philox4x64_10(ctr, key):

@@ -26,6 +26,15 @@ MUTANTS = {
     "daughter_uid_offset": ("st->next_uid + (uint64_t)rank;", "st->next_uid + (uint64_t)rank + 1;"),
     "mother_volume": ("double v1 = (v * rho) / (1.0 + rho);", "double v1 = v / (1.0 + rho);"),
     "clamp_missing": ("if (dn > P->dmax) {", "if (dn > 1e300) {"),
+    "tolerance_base_signed": ("a->scale_abs += fabs(F);", "a->scale_abs += F;"),
+    "tolerance_base_terms": ("a->scale_abs += fabs(F);", "a->scale_abs += kd + gs;"),
+    "removal_no_swaps": ("for (int64_t e = 0; e < swaps; ++e) move_agent(st, to_left[e], to_right[e]);",
+                         "(void)swaps;"),
+    "removal_tail_descending": ("to_left[swaps_left++] = e + new_size;",
+                                "to_left[swaps_left++] = new_size + removed - 1 - e;"),
+    "removal_ghosts_ignored": ("dirty[ndirty++] = G.base[0] + box_linear(g, ox, oy, oz);", "(void)0;"),
+    "death_ignores_behaviour": ("if ((st->beh[i] & BEH_DIE) && P->death_prob > 0.0)", "if (P->death_prob > 0.0)"),
+    "removal_moves_keep_old_uid": ("  st->uid[to] = st->uid[from];\n", "\n"),
 }
 
 
@@ -33,6 +42,12 @@ def _checks():
     c = []
     for row in pins._pair_lines():
         c.append(lambda row=row: pins.test_two_sphere_hand_worked(*row))
+    for row in pins._scale_lines():
+        c.append(lambda row=row: pins.test_tolerance_bases_two_spheres_hand_worked(*row))
+    for row in pins._removal_lines():
+        c.append(lambda row=row: pins.test_parallel_removal_hand_worked(*row))
+    for seed in (1, 2):
+        c.append(lambda seed=seed: pins.test_parallel_removal_invariants(seed))
     for kind in ("uniform", "lattice_ties", "clustered"):
         c.append(lambda kind=kind: pins.test_grid_neighbors_equal_brute_force(kind))
     for key, ctr in [((5, 7), (0, 0, 0, 0)), ((2**64 - 1, 123), (2**64 - 1, 3, 9, 1))]:

@@ -421,3 +421,172 @@ def test_static_old_position_of_a_mover_is_dirty():
     assert s.is_static[0] == 0  # it left, but its position before the last step was next door
     s.step(P)
     assert s.is_static[0] == 1
+
+
+# --------------------------------------------------------------------------- tolerance bases
+def _scale_lines():
+    rows = []
+    with open(os.path.join(GOLD, "pair_force_scales.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(tuple(float(v) for v in line.split()))
+    return rows
+
+
+@pytest.mark.parametrize("r1,r2,d,s_terms,s_pair", _scale_lines())
+def test_tolerance_bases_two_spheres_hand_worked(r1, r2, d, s_terms, s_pair):
+    # the two per-agent tolerance bases the oracle reports, against the
+    # hand-worked single-contact values (both agents see the same contact)
+    P = O.make_params(R=12.0)
+    p = np.array([[10.0, 10.0 + d], [10.0, 10.0], [10.0, 10.0]])
+    s = _state(p, np.array([2 * r1, 2 * r2]))
+    _, nz, _, sc, sa = s.forces_of(P, with_scale=True, with_scale_abs=True)
+    for a in range(2):
+        assert sc[a] == pytest.approx(s_terms, rel=1e-15, abs=0.0)
+        assert sa[a] == pytest.approx(s_pair, rel=1e-15, abs=0.0)
+
+
+def test_tolerance_base_sums_magnitudes_not_the_vector():
+    # middle of three collinear equal spheres: the forces cancel exactly, but
+    # the pair-force magnitudes add
+    P = O.make_params(R=12.0)
+    p = np.array([[0.0, 9.0, 18.0], [5.0, 5.0, 5.0], [5.0, 5.0, 5.0]])
+    s = _state(p, np.full(3, 10.0))
+    f, _, _, sc, sa = s.forces_of(P, with_scale=True, with_scale_abs=True)
+    assert f[:, 1].tolist() == [0.0, 0.0, 0.0]
+    assert sa[1] == 2.0 * (2.0 - math.sqrt(2.5))
+    assert sc[1] == 2.0 * (2.0 + math.sqrt(2.5))
+    assert sa[0] == 2.0 - math.sqrt(2.5) and sa[2] == sa[0]
+
+
+def test_tolerance_bases_equal_brute_force_sums():
+    # every ordered pair enumerated in numpy (no grid), both bases summed over
+    # the contacts of each agent, including adhesive pairs (F < 0)
+    rng = np.random.default_rng(31)
+    n = 400
+    p = rng.uniform(0.0, 45.0, (3, n))
+    d = rng.uniform(8.0, 12.0, n)
+    P = O.make_params(R=12.0)
+    _, nz, _, sc, sa = _state(p, d).forces_of(P, with_scale=True, with_scale_abs=True)
+    diff = p[:, :, None] - p[:, None, :]
+    dist = np.sqrt((diff ** 2).sum(axis=0))
+    r = d * 0.5
+    delta = r[:, None] + r[None, :] - dist
+    mask = (dist < 12.0) & (delta > 0.0)
+    np.fill_diagonal(mask, False)
+    rbar = np.outer(r, r) / (r[:, None] + r[None, :])
+    kd = 2.0 * np.where(mask, delta, 0.0)
+    gs = np.sqrt(rbar * np.where(mask, delta, 0.0))
+    assert np.array_equal(nz, mask.sum(axis=1))
+    assert np.any(mask & (kd - gs < 0.0)) and np.any(mask & (kd - gs > 0.0))
+    np.testing.assert_allclose(sc, np.where(mask, kd + gs, 0.0).sum(axis=1), rtol=1e-13, atol=0.0)
+    np.testing.assert_allclose(sa, np.where(mask, np.abs(kd - gs), 0.0).sum(axis=1), rtol=1e-13, atol=1e-15)
+
+
+# --------------------------------------------------------------------------- parallel removal
+def _removal_lines():
+    rows = []
+    with open(os.path.join(GOLD, "parallel_removal.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                a, b, c = (part.split() for part in line.split("|"))
+                rows.append((int(a[0]), [int(v) for v in b], [int(v) for v in c]))
+    return rows
+
+
+@pytest.mark.parametrize("n,removed,ids", _removal_lines())
+def test_parallel_removal_hand_worked(n, removed, ids):
+    # ids as uids, and every other attribute tied to the id, so that a moved
+    # agent is seen to move whole
+    uid = np.arange(1, n + 1, dtype=np.uint64)
+    p = np.stack([uid * 1.5, uid * 2.5, uid * 3.5]).astype(np.float64)
+    s = _state(p, uid * 0.25 + 8.0, uid=uid, beh=(uid % 4).astype(np.uint8))
+    rm = np.zeros(n, np.uint8)
+    rm[removed] = 1
+    moves = s.remove(rm)
+    assert s.n == len(ids)
+    assert s.uid[: s.n].tolist() == ids
+    u = s.uid[: s.n].astype(np.float64)
+    assert np.array_equal(s.positions(), np.stack([u * 1.5, u * 2.5, u * 3.5]))
+    assert np.array_equal(s.diam[: s.n], u * 0.25 + 8.0)
+    assert np.array_equal(s.beh[: s.n], (s.uid[: s.n] % 4).astype(np.uint8))
+    assert moves == sum(1 for i in removed if i < len(ids))
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_parallel_removal_invariants(seed):
+    # random removal sets: the survivors are exactly the agents not removed,
+    # every survivor left of the new size keeps its slot, the holes are filled
+    # by survivors from the right in ascending order, and the number of moves
+    # equals the number of holes (at most the number removed)
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(50, 400))
+    uid = rng.permutation(n).astype(np.uint64) + 1000
+    p = rng.uniform(0.0, 100.0, (3, n))
+    s = _state(p, np.full(n, 10.0), uid=uid)
+    rm = (rng.random(n) < rng.uniform(0.05, 0.6)).astype(np.uint8)
+    moves = s.remove(rm)
+    m = n - int(rm.sum())
+    assert s.n == m
+    assert sorted(s.uid[:m].tolist()) == sorted(uid[rm == 0].tolist())
+    holes = [i for i in range(m) if rm[i]]
+    tail = [i for i in range(m, n) if not rm[i]]
+    assert moves == len(holes) == len(tail) <= int(rm.sum())
+    for i in range(m):
+        src = i if not rm[i] else tail[holes.index(i)]
+        assert s.uid[i] == uid[src]
+        assert np.array_equal(s.positions()[:, i], p[:, src])
+
+
+def test_death_draw_rate_and_behaviour_bit():
+    # only DIE agents are removed, at the requested rate (binomial bound),
+    # and a removed agent's Philox draw is below the probability
+    n = 20000
+    rng = np.random.default_rng(9)
+    p = rng.uniform(0.0, 4000.0, (3, n))  # sparse: no contacts
+    beh = np.where(np.arange(n) % 2 == 0, 4, 0).astype(np.uint8)
+    s = _state(p, np.full(n, 10.0), beh=beh)
+    P = O.make_params(R=12.0, death_prob=0.1, seed=77)
+    s.step(P)
+    removed = set(range(n)) - set(s.uid[: s.n].tolist())
+    assert all(i % 2 == 0 for i in removed)
+    k = len(removed)
+    mean, sd = 0.1 * n / 2, math.sqrt(n / 2 * 0.1 * 0.9)
+    assert abs(k - mean) < 5 * sd
+    assert s.counters["n_removed"] == k
+    for i in list(removed)[:50]:
+        assert O.uniform(77, i, 0, 3) < 0.1
+    for i in [j for j in range(0, n, 2) if j not in removed][:50]:
+        assert O.uniform(77, i, 0, 3) >= 0.1
+
+
+def test_removal_with_static_skip_is_bit_exact_and_dirties_the_removed_box():
+    # pairs of slightly overlapping agents whose force is below the
+    # adherence: static with one contact.  When one of a pair dies, its box is
+    # dirty next iteration, so its partner is recomputed (contacts 0) instead
+    # of carrying its old contact count; skip == no-skip for positions and
+    # contacts
+    rng = np.random.default_rng(4)
+    g = np.arange(8) * 40.0
+    z, y, x = np.meshgrid(g, g, g, indexing="ij")
+    c = np.stack([x.ravel(), y.ravel(), z.ravel()]) + 100.0
+    m = c.shape[1]
+    off = np.array([[9.99], [0.0], [0.0]])
+    p = np.concatenate([c, c + off], axis=1)
+    n = p.shape[1]
+    beh = np.concatenate([np.full(m, 4, np.uint8), np.zeros(m, np.uint8)])
+    P_skip = O.make_params(R=12.0, adherence=1.0, detect_static=1, death_prob=0.2, seed=5)
+    P_full = O.make_params(R=12.0, adherence=1.0, detect_static=0, death_prob=0.2, seed=5)
+    a = _state(p, np.full(n, 10.0), beh=beh)
+    b = _state(p, np.full(n, 10.0), beh=beh)
+    partner_freed = 0
+    for t in range(6):
+        a.step(P_skip)
+        b.step(P_full)
+        assert np.array_equal(a.uid[: a.n], b.uid[: b.n])
+        assert np.array_equal(a.positions(), b.positions())
+        assert np.array_equal(a.nz[: a.n], b.nz[: b.n]), "contacts differ after step %d" % (t + 1)
+        partner_freed += int(((b.nz[: b.n] == 0) & (b.uid[: b.n] >= m)).sum())
+    assert a.counters["n_static"] > 0 and partner_freed > 0
