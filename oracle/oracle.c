@@ -22,6 +22,9 @@
  *   Sec. 5  defers the pair force to Cortex3D without a formula; the force
  *   used here is F = k*delta - gamma*sqrt(rbar*delta) along the centre line,
  *   delta = r_i + r_j - d, rbar = r_i r_j / (r_i + r_j), k = 2, gamma = 1.
+ *   Sec. 6.5 (cell sorting, differential adhesion between cell types)  ->
+ *   with n_types > 1 the pair's constants are k and gamma of its two types,
+ *   the type being bits 4-5 of the agent's behaviour byte.
  *
  * Pins (tests/test_oracle_pins.py): brute-force O(N^2) neighbour sets, the
  * hand-worked two/three-sphere forces, antisymmetry, translation invariance,
@@ -46,6 +49,7 @@
 #define BEH_GROW 1u
 #define BEH_WALK 2u
 #define BEH_DIE 4u
+#define TYPE_OF(beh) (((beh) >> 4) & 3u)
 
 typedef struct {
   double R;          /* interaction radius: neighbour iff d^2 < R^2, j != i   */
@@ -62,6 +66,10 @@ typedef struct {
   double walk_step;      /* random-walk step length for WALK agents             */
   uint64_t seed;
   double death_prob;     /* per-iteration probability that a DIE agent is removed */
+  int32_t n_types;       /* > 1: per-type-pair force constants below              */
+  int32_t pad;
+  double type_k[16];     /* k of the types (a, b) at [4 a + b]                    */
+  double type_gamma[16]; /* gamma of the types (a, b) at [4 a + b]                */
 } orc_params;
 
 typedef struct {
@@ -453,7 +461,13 @@ static void force_on(const orc_state *st, const orc_params *P, const grid_t *G, 
           double delta = (ri + rj) - d;
           if (!(delta > 0.0)) continue;
           double rbar = (ri * rj) / (ri + rj);
-          double kd = P->k * delta, gs = P->gamma * sqrt(rbar * delta);
+          double k = P->k, gamma = P->gamma;
+          if (P->n_types > 1) {
+            const unsigned ab = 4u * TYPE_OF(st->beh[i]) + TYPE_OF(st->beh[j]);
+            k = P->type_k[ab];
+            gamma = P->type_gamma[ab];
+          }
+          double kd = k * delta, gs = gamma * sqrt(rbar * delta);
           double F = kd - gs;
           double sc = F / d;
           a->scale += kd + gs;

@@ -51,7 +51,8 @@ class Params(C.Structure):
         ("detect_static", C.c_int32), ("sort_every", C.c_int32),
         ("growth", C.c_double), ("divide_volume", C.c_double),
         ("ratio_lo", C.c_double), ("ratio_hi", C.c_double), ("walk_step", C.c_double),
-        ("seed", C.c_uint64), ("death_prob", C.c_double),
+        ("seed", C.c_uint64), ("death_prob", C.c_double), ("n_types", C.c_int32), ("pad", C.c_int32),
+        ("type_k", C.c_double * 16), ("type_gamma", C.c_double * 16),
     ]
 
 
@@ -116,6 +117,8 @@ DEFAULTS = dict(R=12.0, L=0.0, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.
 
 
 def make_params(**kw) -> Params:
+    """Oracle parameters; type_k / type_gamma (n_types x n_types nested
+    lists or arrays) set the per-type-pair force constants."""
     d = dict(DEFAULTS)
     for k, v in kw.items():
         if k in d:
@@ -125,6 +128,13 @@ def make_params(**kw) -> Params:
     p = Params()
     for k, v in d.items():
         setattr(p, k, v)
+    if kw.get("type_k") is not None:
+        tk, tg = np.asarray(kw["type_k"], np.float64), np.asarray(kw["type_gamma"], np.float64)
+        p.n_types = tk.shape[0]
+        for a in range(tk.shape[0]):
+            for b in range(tk.shape[1]):
+                p.type_k[4 * a + b] = tk[a, b]
+                p.type_gamma[4 * a + b] = tg[a, b]
     return p
 
 

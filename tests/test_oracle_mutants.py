@@ -35,6 +35,10 @@ MUTANTS = {
     "removal_ghosts_ignored": ("dirty[ndirty++] = G.base[0] + box_linear(g, ox, oy, oz);", "(void)0;"),
     "death_ignores_behaviour": ("if ((st->beh[i] & BEH_DIE) && P->death_prob > 0.0)", "if (P->death_prob > 0.0)"),
     "removal_moves_keep_old_uid": ("  st->uid[to] = st->uid[from];\n", "\n"),
+    "type_pair_own_type_twice": ("4u * TYPE_OF(st->beh[i]) + TYPE_OF(st->beh[j])",
+                                 "4u * TYPE_OF(st->beh[i]) + TYPE_OF(st->beh[i])"),
+    "type_gamma_from_k_table": ("gamma = P->type_gamma[ab];", "gamma = P->type_k[ab];"),
+    "type_bits_shifted": ("#define TYPE_OF(beh) (((beh) >> 4) & 3u)", "#define TYPE_OF(beh) (((beh) >> 3) & 3u)"),
 }
 
 
@@ -48,6 +52,8 @@ def _checks():
         c.append(lambda row=row: pins.test_parallel_removal_hand_worked(*row))
     for seed in (1, 2):
         c.append(lambda seed=seed: pins.test_parallel_removal_invariants(seed))
+    for row in pins._hetero_lines():
+        c.append(lambda row=row: pins.test_heterotypic_two_spheres_hand_worked(*row))
     for kind in ("uniform", "lattice_ties", "clustered"):
         c.append(lambda kind=kind: pins.test_grid_neighbors_equal_brute_force(kind))
     for key, ctr in [((5, 7), (0, 0, 0, 0)), ((2**64 - 1, 123), (2**64 - 1, 3, 9, 1))]:

@@ -590,3 +590,60 @@ def test_removal_with_static_skip_is_bit_exact_and_dirties_the_removed_box():
         assert np.array_equal(a.nz[: a.n], b.nz[: b.n]), "contacts differ after step %d" % (t + 1)
         partner_freed += int(((b.nz[: b.n] == 0) & (b.uid[: b.n] >= m)).sum())
     assert a.counters["n_static"] > 0 and partner_freed > 0
+
+
+# --------------------------------------------------------------------------- heterotypic adhesion
+TYPE_K = [[2.0, 1.5], [1.5, 3.0]]
+TYPE_GAMMA = [[1.0, 0.5], [0.5, 2.0]]
+
+
+def _hetero_lines():
+    rows = []
+    with open(os.path.join(GOLD, "heterotypic_pair_forces.txt")) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                v = line.split()
+                rows.append((int(v[0]), int(v[1])) + tuple(float(x) for x in v[2:]))
+    return rows
+
+
+@pytest.mark.parametrize("t1,t2,r1,r2,d,F", _hetero_lines())
+def test_heterotypic_two_spheres_hand_worked(t1, t2, r1, r2, d, F):
+    P = O.make_params(R=12.0, type_k=TYPE_K, type_gamma=TYPE_GAMMA)
+    u = np.array([2.0, -1.0, 2.0]) / 3.0
+    p = np.array([[10.0, 10.0, 10.0], [10.0, 10.0, 10.0] + d * u]).T
+    beh = np.array([t1 << 4, t2 << 4], np.uint8)
+    f, nz, _ = _state(p, np.array([2 * r1, 2 * r2]), beh=beh).forces_of(P)
+    assert nz.tolist() == [1, 1]
+    assert np.allclose(f[:, 0], -F * u, rtol=0, atol=1e-14)
+    assert np.allclose(f[:, 1], F * u, rtol=0, atol=1e-14)
+
+
+def test_uniform_type_table_equals_one_type_bit_exact():
+    # every type pair given the one-type constants: the same forces, bit for bit
+    rng = np.random.default_rng(12)
+    n = 1500
+    p = rng.normal(60.0, 10.0, (3, n))
+    d = rng.uniform(8.0, 12.0, n)
+    beh = (rng.integers(0, 4, n) << 4).astype(np.uint8)
+    s = _state(p, d, beh=beh)
+    f1, nz1, _ = s.forces_of(O.make_params(R=12.0))
+    f4, nz4, _ = s.forces_of(O.make_params(R=12.0, type_k=np.full((4, 4), 2.0), type_gamma=np.full((4, 4), 1.0)))
+    assert np.array_equal(f1, f4) and np.array_equal(nz1, nz4) and nz1.sum() > 0
+
+
+def test_heterotypic_antisymmetry_and_type_dependence():
+    # a symmetric table keeps the pair forces antisymmetric (net internal force
+    # vanishes); swapping which agents carry which type changes the forces
+    rng = np.random.default_rng(13)
+    n = 800
+    p = rng.normal(50.0, 8.0, (3, n))
+    d = rng.uniform(8.0, 12.0, n)
+    beh = (rng.integers(0, 2, n) << 4).astype(np.uint8)
+    P = O.make_params(R=12.0, type_k=TYPE_K, type_gamma=TYPE_GAMMA)
+    f, nz, _ = _state(p, d, beh=beh).forces_of(P)
+    scale = np.abs(f).sum()
+    assert np.abs(f.sum(axis=1)).max() <= 1e-12 * scale
+    f_sw, _, _ = _state(p, d, beh=(beh ^ 0x10).astype(np.uint8)).forces_of(P)
+    assert not np.array_equal(f, f_sw) and nz.sum() > 0
