@@ -28,16 +28,24 @@ sys.path.insert(0, ROOT)
 METRIC = "agent-updates/s per mechanical step, FP32-force vs plain FP64 form; % HBM peak"
 UNIT = "agent-updates/s"
 SM_COUNT, FP32_LANES_PER_SM, SM_MAX_MHZ = 152, 128, 2070.0
-# algorithmic FP32 work of the force kernel: 8 flops per candidate pair
-# (3 differences, 3 products, 2 sums for d^2) and 20 per contact (radius sum
-# and square, inverse root and distance, overlap, reduced radius, the two force
-# terms and their difference, the scale and three fused accumulations)
-FLOPS_PER_CANDIDATE, FLOPS_PER_CONTACT = 8, 20
+# algorithmic FP32 work of the force kernel, two models:
+#  - the scope table's: 10 flops per candidate pair (the prefilter) and 25 per
+#    contact (the force), the model the reported fraction uses;
+#  - a tighter count of the kernel's own arithmetic: 8 per candidate (3
+#    differences, 3 products, 2 sums for d^2) and 20 per contact (radius sum
+#    and square, inverse root and distance, overlap, reduced radius, the two
+#    force terms and their difference, the scale and three fused
+#    accumulations), reported beside it
+FLOP_MODEL = (10, 25)
+FLOP_MODEL_KERNEL = (8, 20)
 # algorithmic HBM bytes per agent of the force kernel in the FP32 form: own
 # record (16) + sorted->storage index (4) + flags and contacts in/out (6) +
 # position read (24) and write (24)
 FORCE_BYTES_PER_AGENT = 74
-PROFILE_FILE = os.path.join(ROOT, "profiles", "force_fp32_blobs10M.md")
+# DRAM traffic of the force kernel from an ncu capture, keyed by the hash of
+# the kernel's sources (used only while they match the source that runs)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "k_force_fp32_traffic.json")
+HBM_FALLBACK_GBS = 6800.0
 
 
 def parse():
@@ -58,6 +66,8 @@ def parse():
     ap.add_argument("--presort", action="store_true",
                     help="blobs: put storage in Morton order (bdm_sort) before the warm-up")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble, core_shell: skip the autotuner")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="blobs: skip the compact ensemble and core + shell legs of the default line")
     return ap.parse_args()
 
 
@@ -148,64 +158,103 @@ def force_source_sha():
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
-    """dram bytes per force launch from the committed ncu summary, if it was
-    taken on the current kernel source."""
+def committed_traffic(n_agents):
+    """DRAM bytes of one force launch over n_agents, from the machine-readable
+    record of an ncu capture (bytes per agent), if that capture was taken on
+    the current kernel source; else None."""
     try:
-        text = open(PROFILE_FILE).read()
-    except OSError:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
         return None, None
-    m_sha = re.search(r"source_sha256:\s*([0-9a-f]+)", text)
-    m_b = re.search(r"dram_bytes_per_launch_full:\s*([0-9.eE+]+)", text)
-    if not m_sha or not m_b or m_sha.group(1) != force_source_sha():
-        return None, (m_sha.group(1) if m_sha else None)
-    return float(m_b.group(1)), m_sha.group(1)
+    if rec.get("source_sha256") != force_source_sha():
+        return None, rec.get("source_sha256")
+    return float(rec["dram_bytes_per_agent"]) * n_agents, rec["source_sha256"]
 
 
 def measured_peaks():
+    """Measured peaks (HBM copy GB/s, ...), or the profiling recipe's fallback
+    HBM figure when the measured file is absent."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return json.load(f)
-    except OSError:
-        return {}
+            d = json.load(f)
+            d["_source"] = "of measured"
+            return d
+    except (OSError, ValueError):
+        return {"hbm_gbs": HBM_FALLBACK_GBS, "_source": "of fallback"}
 
 
-def cpu_baseline(n_sample, n_steps=1):
-    """The FP64 oracle, as it stands, on one host core over a same-density
-    sample of the blob workload."""
+def oracle_timing_lib():
+    """The oracle's OpenMP timing build (all host cores) and its thread count,
+    or the serial build and 1."""
+    from oracle import build_oracle
+    from oracle import oracle as O
+    path = build_oracle.build_omp()
+    if path is None:
+        O.lib()
+        return None, 1
+    return path, None
+
+
+def cpu_baseline(n_sample, n_steps=2):
+    """The FP64 oracle, as it stands (its OpenMP timing build: the per-agent
+    force loop over all host cores, same results), over a same-density sample
+    of the blob workload.  Returns agent-updates/s, seconds, threads."""
     from oracle import oracle as O
     w = workload(n_sample)
     P = O.make_params(R=11.0, L=11.0, dt=0.01, dmax=3.0, sort_every=10, seed=3)
-    s = O.State(w.x, w.y, w.z, w.diam)
-    O.lib()
-    t0 = time.perf_counter()
-    s.step(P, n_steps)
-    dt = time.perf_counter() - t0
-    return n_sample * n_steps / dt, dt
+    path, _ = oracle_timing_lib()
+    lib = O.use_library(path) if path else None
+    if lib is not None:
+        L = lib.__enter__()
+        threads = L.orc_threads()
+    else:
+        threads = 1
+    try:
+        s = O.State(w.x, w.y, w.z, w.diam)
+        t0 = time.perf_counter()
+        s.step(P, n_steps)
+        dt = time.perf_counter() - t0
+    finally:
+        if lib is not None:
+            lib.__exit__(None, None, None)
+    return n_sample * n_steps / dt, dt, threads
 
 
 # ---------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    n_s = args.sample or int(min(1_000_000, max(100_000, 1.5e7 / max(1, args.steps + args.warmup))))
+    n_s = args.sample or int(min(2_000_000, max(200_000, 6e7 / max(1, args.steps + args.warmup))))
     from oracle import oracle as O
     w = workload(n_s)
     P = O.make_params(R=11.0, L=11.0, dt=0.01, dmax=3.0, sort_every=10, seed=3)
-    s = O.State(w.x, w.y, w.z, w.diam)
-    O.lib()
-    s.step(P, args.warmup)
-    t0 = time.perf_counter()
-    s.step(P, args.steps)
-    dt = time.perf_counter() - t0
+    path, _ = oracle_timing_lib()
+    lib = O.use_library(path) if path else None
+    threads = lib.__enter__().orc_threads() if lib is not None else 1
+    try:
+        s = O.State(w.x, w.y, w.z, w.diam)
+        s.step(P, args.warmup)
+        t0 = time.perf_counter()
+        s.step(P, args.steps)
+        dt = time.perf_counter() - t0
+    finally:
+        if lib is not None:
+            lib.__exit__(None, None, None)
     v = n_s * args.steps / dt
+    cfg = config(args)
+    cfg["n_agents"] = n_s
+    cfg["workload"] = ("blobs-%d (a same-density sample of the %d-agent workload: lengths scaled by "
+                       "(n/1e7)^(1/3)): 8 Gaussian blobs, diameters U[9,11] um, R = L = 11 um, dt 0.01, "
+                       "max displacement 3 um, Morton re-sort every 10 iterations" % (n_s, args.n))
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config(args),
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": "%d iterations of the FP64 oracle over a %d-agent blob workload of the same "
-                                   "density (lengths scaled by (n/1e7)^(1/3)), one host core" % (args.steps, n_s)},
+                                   "density, force loop on %d host threads (OpenMP timing build)"
+                                   % (args.steps, n_s, threads)},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -339,6 +388,98 @@ def run_other(args):
     return 0
 
 
+# ---------------------------------------------------------------- compact legs of the default line
+# Settings the autotuner picked for these workloads (box edge, kernel lanes:
+# -1 = per-box cost model, sort cadence); the legs use them without re-tuning
+# so that the default run stays short.
+ENSEMBLE_SETTINGS = dict(box_edge=15.0, lanes=-1, sort_every=10)
+CORE_SHELL_SETTINGS = dict(box_edge=15.0, lanes=-1, sort_every=5)
+
+
+def leg_ensemble(args, steps=10, warmup=3):
+    """512 independent simulations: one launch sequence per iteration for all
+    members (batched) against one per member, agent-updates/s of each."""
+    import torch
+
+    from paper_2301_06984_gb300 import bdm
+    from paper_2301_06984_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    w = W.ensemble()
+    st = ENSEMBLE_SETTINGS
+    sim = bdm.Simulation.from_workload(w, box_edge=st["box_edge"], sort_every=st["sort_every"])
+    sim.set_force_kernel(st["lanes"])
+    sim.set_workload(w)
+    sim.step(warmup)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = timed_steps(sim, steps, stream)
+    sims = []
+    for m in range(w.n_sims):
+        lo, hi = w.sim_off[m], w.sim_off[m + 1]
+        q = bdm.Simulation(R=10.0, capacity=int(hi - lo), dt=float(w.dt_sim[m]), precision="fp32",
+                           box_edge=st["box_edge"], sort_every=st["sort_every"])
+        q.set_force_kernel(st["lanes"])
+        q.set_agents(w.x[lo:hi], w.y[lo:hi], w.z[lo:hi], w.diam[lo:hi])
+        q.step(warmup)
+        sims.append(q)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k1 = max(1, steps // 2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for q in sims:
+        q.step(k1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms1 = e0.elapsed_time(e1)
+    for q in sims:
+        q.close()
+    sim.close()
+    batched = w.n * steps / (ms * 1e-3)
+    per_sim = w.n * k1 / (ms1 * 1e-3)
+    return {"workload": "ensemble-512: 512 simulations, 10^U[3,5] agents each (%d in all), d = 10 um, dt "
+                        "U[0.005,0.02], FP32 form" % w.n, "settings": st, "steps": steps, "warmup": warmup,
+            "batched": {"value": batched, "unit": UNIT, "ms_per_step": ms / steps},
+            "one_launch_sequence_per_simulation": {"value": per_sim, "unit": UNIT, "ms_per_step": ms1 / k1,
+                                                   "steps": k1},
+            "batched_speedup": batched / per_sim, "clocks": clk.summary()}
+
+
+def leg_core_shell(args, steps=10, warmup=3):
+    """150M agents, 90% in a static core: agent-updates/s, the skipped
+    fraction, per-phase times and the algorithmic HBM throughput of the
+    iteration."""
+    import torch
+
+    from paper_2301_06984_gb300 import bdm
+    from paper_2301_06984_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    w = W.core_shell()
+    st = CORE_SHELL_SETTINGS
+    sim = bdm.Simulation.from_workload(w, box_edge=st["box_edge"], sort_every=st["sort_every"])
+    sim.set_force_kernel(st["lanes"])
+    sim.set_workload(w)
+    sim.step(warmup)
+    c0 = sim.counters()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        ms = timed_steps(sim, steps, stream)
+    c = sim.counters()
+    sim.profile_begin()
+    sim.step(2)
+    phases = sim.profile_end()
+    sim.close()
+    stat = c["n_static"]
+    bytes_step = STEP_BYTES_MOVING * (w.n - stat) + STEP_BYTES_STATIC * stat
+    peaks = measured_peaks()
+    gbs = bytes_step / (ms / steps * 1e-3) / 1e9
+    return {"workload": "core_shell-150M: FCC static core (90%%) + random-walk shell (10%%), d = 10 um, R = 10 um, "
+                        "static-agent skip on, FP32 form (%d agents)" % w.n, "settings": st, "steps": steps,
+            "warmup": warmup, "value": w.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+            "skipped_fraction": stat / w.n,
+            "hbm": {"bytes_per_step_algorithmic": bytes_step, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
+                    "frac": gbs / peaks["hbm_gbs"], "peak_source": peaks["_source"]},
+            "phases_ms_per_step": {k: round(v[0] / 2, 4) for k, v in phases.items()},
+            "gpu_launches": c["kernels_launched"] - c0["kernels_launched"], "clocks": clk.summary()}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -405,19 +546,25 @@ def main():
         agents += c["n_agents"]
     phases = sim.profile_end()
     force_ms = phases["force"][0] / kp
-    flops = (FLOPS_PER_CANDIDATE * cand + FLOPS_PER_CONTACT * cont) / kp
+    flops = (FLOP_MODEL[0] * cand + FLOP_MODEL[1] * cont) / kp
+    flops_k = (FLOP_MODEL_KERNEL[0] * cand + FLOP_MODEL_KERNEL[1] * cont) / kp
     clocks = clk.summary()
     peak_alu = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
     achieved = flops / (force_ms * 1e-3) / 1e12
-    traffic, sha = committed_traffic()
+    traffic, sha = committed_traffic(agents / kp)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    roofline = {"bound": "alu", "kernel": "k_force<FP32,STEP> (lane-per-agent force kernel, 4 lanes per agent)", "achieved": achieved, "peak": peak_alu,
-                "unit": "TFLOP/s", "frac": achieved / peak_alu, "traffic": traffic,
+    roofline = {"bound": "alu", "kernel": "k_force<FP32,STEP> (lane-per-agent force kernel, 4 lanes per agent)",
+                "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s", "frac": achieved / peak_alu,
+                "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal, derived)",
-                "flops_per_launch": flops,
+                "flop_model": "%d per candidate pair, %d per contact" % FLOP_MODEL, "flops_per_launch": flops,
+                "kernel_flop_model": {"per_candidate": FLOP_MODEL_KERNEL[0], "per_contact": FLOP_MODEL_KERNEL[1],
+                                      "achieved": flops_k / (force_ms * 1e-3) / 1e12,
+                                      "frac": flops_k / (force_ms * 1e-3) / 1e12 / peak_alu},
                 "hbm_view": {"achieved_gbs": FORCE_BYTES_PER_AGENT * agents / kp / (force_ms * 1e-3) / 1e9,
-                             "peak_gbs": hbm, "peak_source": "of measured" if hbm else None}}
+                             "frac": FORCE_BYTES_PER_AGENT * agents / kp / (force_ms * 1e-3) / 1e9 / hbm,
+                             "peak_gbs": hbm, "peak_source": peaks["_source"]}}
     phase_ms = {k: round(v[0] / kp, 4) for k, v in phases.items()}
 
     line = {
@@ -426,7 +573,8 @@ def main():
         "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(args),
         "gpu_launches": launches, "clocks": clocks, "roofline": roofline, "phases_ms_per_step": phase_ms,
         "counters_last_step": {k: c1[k] for k in ("n_agents", "n_candidates", "n_neighbors", "n_contacts",
-                                                  "n_exact_fallback", "n_occupied_bricks", "max_brick_agents")},
+                                                  "n_exact_fallback", "n_fp64_fixup", "n_occupied_bricks",
+                                                  "max_brick_agents")},
     }
 
     # ---- plain FP64 form on the same workload
@@ -479,14 +627,19 @@ def main():
                        "h2d_bytes_per_step": 32 * n, "d2h_bytes_per_step": 24 * n, "steps": ke}
         se.close()
 
+    # ---- the other two throughput configurations, compact (N = 1 only)
+    if world == 1 and not args.no_legs:
+        line["ensemble_leg"] = leg_ensemble(args)
+        line["core_shell_leg"] = leg_core_shell(args)
+
     # ---- FP64 oracle on the host cores (rank 0, N = 1 only)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n_s = args.sample or 1_000_000
-        v, dt = cpu_baseline(n_s)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "one iteration of the FP64 oracle over a %d-agent blob workload of the "
-                                          "same density (lengths scaled by (n/1e7)^(1/3)), %.1f s on one host "
-                                          "core" % (n_s, dt)}
+        n_s = args.sample or 2_000_000
+        v, dt, threads = cpu_baseline(n_s)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": "2 iterations of the FP64 oracle over a %d-agent blob workload of the "
+                                          "same density (lengths scaled by (n/1e7)^(1/3)), %.1f s, force loop on "
+                                          "%d host threads (OpenMP timing build)" % (n_s, dt, threads)}
     if rank == 0:
         print(json.dumps(line), flush=True)
     sim.close()

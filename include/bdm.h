@@ -65,6 +65,8 @@ extern "C" {
 /* per-agent behaviour bits */
 #define BDM_BEH_GROW 1u /* volume += growth_per_step; divide at divide_volume     */
 #define BDM_BEH_WALK 2u /* random walk of walk_step um after the clamp            */
+#define BDM_BEH_DIE 4u  /* removed with probability death_prob per iteration     */
+#define BDM_TYPE_SHIFT 4 /* bits 4-5 of the behaviour byte: the agent's type (0-3) */
 
 typedef struct bdm_sim bdm_sim;
 
@@ -88,6 +90,17 @@ typedef struct {
   int64_t capacity;          /* maximum number of agents, daughters included          */
   int32_t keep_forces;       /* 1: keep each iteration's summed forces (debug output) */
   int32_t reserved;
+  double death_prob;         /* probability that a BDM_BEH_DIE agent is removed in an
+                                iteration (0 = no removal)                           */
+  int32_t n_types;           /* 0 or 1: k and gamma for every pair; 2..4: the pair of
+                                agent types (a, b) uses type_k[4 a + b] and
+                                type_gamma[4 a + b] (Sec. 6.5 cell sorting:
+                                differential adhesion); the type is bits 4-5 of
+                                the agent's behaviour byte (BDM_TYPE_SHIFT)          */
+  int32_t reserved2;
+  double type_k[16];         /* symmetric, finite, >= 0 over the first n_types rows;
+                                entries of types >= n_types are used as given       */
+  double type_gamma[16];
 } bdm_params;
 
 typedef struct {
@@ -108,6 +121,8 @@ typedef struct {
   int64_t kernels_launched;   /* CUDA kernels this simulation has launched so far   */
   int32_t history_valid;      /* static detection has the previous iteration       */
   int32_t error;              /* sticky device error word (0 = none)               */
+  int64_t n_removed;          /* agents removed in the last iteration              */
+  int64_t n_fp64_fixup;       /* FP32 form: agents the FP64 fix-up pass evaluated  */
 } bdm_counters;
 
 /* Create a simulation: the parameters of the paper's problem statement
@@ -213,10 +228,9 @@ int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out
 /* Autotuner.  Times `trial_steps` iterations of the production path (after
  * one warm-up iteration) for each candidate setting, restoring the state
  * before every trial, and keeps the fastest: the box edge L in {R, 1.125 R,
- * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel in {lane-per-agent
- * kernel with 4 lanes per agent, pair-ring kernel, lane-per-agent kernel with
- * the per-box cost model, with 2 lanes, with 8 lanes} (BDM_TUNE_LANES; the
- * values of bdm_set_force_kernel), and the sort
+ * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel's lanes per
+ * agent in {4, the per-box cost model, 2, 8} (BDM_TUNE_LANES; the values of
+ * bdm_set_force_kernel), and the sort
  * cadence in {current, 0, 5, 10, 20} (BDM_TUNE_SORT), one dimension after the
  * other.  The state (agents, step, uid counter) is the same afterwards; the
  * static-detection history starts empty.  Changing L keeps neighbour sets
@@ -240,9 +254,7 @@ int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
  * the lane-per-agent kernel: a warp takes a box's agents, that many lanes
  * split each agent's candidates, and each lane queues its prefiltered pairs
  * before evaluating them.  lanes = -1 selects the same kernel with the lanes
- * chosen per box by a cost model.  lanes = 0 selects the pair-ring kernel: per
- * box the warp tests 32 candidates per instruction, queues the pairs inside
- * the cutoff band and evaluates them 32 at a time.  All give the same
+ * chosen per box by a cost model.  All give the same
  * neighbour and contact decisions (FP64-exact) and forces within the
  * FP32-form tolerance; the choice takes effect at the next iteration.  No
  * effect on the FP64 form.  Errors: BDM_EINVAL (other lanes values). */
@@ -258,8 +270,9 @@ int bdm_profile_begin(bdm_sim *sim);
 int bdm_profile_end(bdm_sim *sim, double *ms, int64_t *launches, int cap, int *n_phases);
 
 /* Name of phase `phase` (0-based) of an iteration: "geometry", "brick_rank",
- * "keys", "brick_scan", "scatter", "brick_sort", "gather", "force", "divide",
- * "finish"; "" outside the range. */
+ * "keys", "brick_scan", "scatter", "brick_sort", "gather", "force",
+ * "force_fix" (the FP32 form's FP64 fix-up pass), "divide" (division merge
+ * and removal), "finish"; "" outside the range. */
 const char *bdm_phase_name(int phase);
 
 /* Change the stream all later work of this simulation is ordered on. */

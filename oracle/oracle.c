@@ -37,6 +37,9 @@
  * die (a Philox draw per agent and iteration) has no printed reference.
  */
 #include <math.h>
+#ifdef ORC_OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -601,6 +604,16 @@ int64_t orc_neighbors_brute(const orc_state *st, const orc_params *P, int64_t *o
   return total;
 }
 
+/* Threads the force loops run on: 1, or the OpenMP thread count of the
+ * timing build. */
+int orc_threads(void) {
+#ifdef ORC_OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
 /* Summed pair force on selected agents (all when q == NULL), without the
  * static skip; f is 3 x nq SoA.  Optional outputs: nz (contacts), nnb
  * (neighbours), scale (sum over contacts of the magnitudes of the two force
@@ -818,18 +831,22 @@ int orc_step(orc_state *st, const orc_params *P) {
     return ORC_ENOMEM;
   }
   double *ny = nx + n, *nzp = nx + 2 * n;
-  st->n_static = 0;
-  st->n_coincident = 0;
+  int64_t n_static = 0, n_coincident = 0;
+  /* each agent's sum is serial in the canonical order, so the timing build's
+   * parallel loop (ORC_OPENMP) gives the same bits as the serial one */
+#ifdef ORC_OPENMP
+#pragma omp parallel for schedule(dynamic, 256) reduction(+ : n_static, n_coincident)
+#endif
   for (int64_t i = 0; i < n; ++i) {
     double dxv = 0.0, dyv = 0.0, dzv = 0.0;
     double fxv = 0.0, fyv = 0.0, fzv = 0.0;
     if (stat[i]) {
       nnz[i] = st->nz[i];
-      st->n_static++;
+      n_static++;
     } else {
       force_acc a;
       force_on(st, P, &G, i, &a, NULL, NULL);
-      st->n_coincident += a.ncoincident;
+      n_coincident += a.ncoincident;
       nnz[i] = a.nz;
       fxv = a.fx; fyv = a.fy; fzv = a.fz;
       double fn = sqrt((a.fx * a.fx + a.fy * a.fy) + a.fz * a.fz);
@@ -858,6 +875,8 @@ int orc_step(orc_state *st, const orc_params *P) {
     if (st->fx) { st->fx[i] = fxv; st->fy[i] = fyv; st->fz[i] = fzv; }
     if (st->is_static) st->is_static[i] = stat[i];
   }
+  st->n_static = n_static;
+  st->n_coincident = n_coincident;
   free(stat);
   free(dirty);
 

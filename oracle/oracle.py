@@ -105,6 +105,8 @@ def _declare(L):
     L.orc_morton3.restype = C.c_uint64
     L.orc_morton2.argtypes = [C.c_uint64, C.c_uint64]
     L.orc_morton2.restype = C.c_uint64
+    L.orc_threads.argtypes = []
+    L.orc_threads.restype = C.c_int
     L.orc_remove.argtypes = [SP, vp]
     L.orc_remove.restype = C.c_int64
     L.orc_morton_offsets.argtypes = [C.c_int32, vp, vp, vp, C.c_int64]

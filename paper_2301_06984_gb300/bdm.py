@@ -15,7 +15,8 @@ from . import build as _build
 BDM_OK, BDM_EINVAL, BDM_ENOMEM, BDM_ECUDA, BDM_ECAPACITY, BDM_ETIMEOUT, BDM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 BDM_FP64, BDM_FP32_FORCE = 0, 1
 BDM_HOST, BDM_DEVICE = 0, 1
-BEH_GROW, BEH_WALK = 1, 2
+BEH_GROW, BEH_WALK, BEH_DIE = 1, 2, 4
+TYPE_SHIFT = 4  # bits 4-5 of the behaviour byte: the agent's type
 DBG_FORCES, DBG_NZ, DBG_STATIC, DBG_GRID_BOX, DBG_GRID_ORDER = 1, 2, 3, 4, 5
 DBG_GRID_GEOMETRY, DBG_BRICK_RANK, DBG_NEIGHBORS, DBG_FORCES_NOW = 6, 7, 8, 9
 
@@ -37,7 +38,9 @@ class Params(C.Structure):
         ("dt_per_sim", C.POINTER(C.c_double)), ("seed", C.c_uint64),
         ("growth_per_step", C.c_double), ("divide_volume", C.c_double), ("ratio_lo", C.c_double),
         ("ratio_hi", C.c_double), ("walk_step", C.c_double), ("capacity", C.c_int64),
-        ("keep_forces", C.c_int32), ("reserved", C.c_int32),
+        ("keep_forces", C.c_int32), ("reserved", C.c_int32), ("death_prob", C.c_double),
+        ("n_types", C.c_int32), ("reserved2", C.c_int32), ("type_k", C.c_double * 16),
+        ("type_gamma", C.c_double * 16),
     ]
 
 
@@ -56,7 +59,7 @@ class Counters(C.Structure):
         ("n_neighbors", C.c_int64), ("n_contacts", C.c_int64), ("n_exact_fallback", C.c_int64),
         ("n_boxes", C.c_int64), ("n_bricks", C.c_int64), ("n_occupied_bricks", C.c_int64),
         ("max_brick_agents", C.c_int64), ("kernels_launched", C.c_int64), ("history_valid", C.c_int32),
-        ("error", C.c_int32),
+        ("error", C.c_int32), ("n_removed", C.c_int64), ("n_fp64_fixup", C.c_int64),
     ]
 
     def as_dict(self):
@@ -130,7 +133,7 @@ class Simulation:
     def __init__(self, R, capacity, box_edge=0.0, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.0,
                  precision="fp64", detect_static=False, sort_every=0, n_sims=1, dt_per_sim=None, seed=0,
                  growth=0.0, divide_volume=0.0, ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, keep_forces=False,
-                 stream=None):
+                 death_prob=0.0, type_k=None, type_gamma=None, stream=None):
         L = lib()
         p = Params()
         p.interaction_radius = R
@@ -156,6 +159,14 @@ class Simulation:
         p.walk_step = walk_step
         p.capacity = int(capacity)
         p.keep_forces = int(bool(keep_forces))
+        p.death_prob = death_prob
+        if type_k is not None:
+            tk, tg = np.asarray(type_k, np.float64), np.asarray(type_gamma, np.float64)
+            p.n_types = tk.shape[0]
+            for a in range(tk.shape[0]):
+                for b in range(tk.shape[1]):
+                    p.type_k[4 * a + b] = tk[a, b]
+                    p.type_gamma[4 * a + b] = tg[a, b]
         self.params = p
         self.n_sims = int(n_sims)
         self.precision = p.precision
@@ -185,7 +196,8 @@ class Simulation:
                   sort_every=p.get("sort_every", 0), n_sims=w.n_sims, dt_per_sim=w.dt_sim,
                   seed=p.get("seed", 0), growth=p.get("growth", 0.0), divide_volume=p.get("divide_volume", 0.0),
                   ratio_lo=p.get("ratio_lo", 0.9), ratio_hi=p.get("ratio_hi", 1.1),
-                  walk_step=p.get("walk_step", 0.0))
+                  walk_step=p.get("walk_step", 0.0), death_prob=p.get("death_prob", 0.0),
+                  type_k=p.get("type_k"), type_gamma=p.get("type_gamma"))
         kw.update(over)
         return cls(capacity=capacity or w.n, **kw)
 
@@ -296,9 +308,8 @@ class Simulation:
         return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
 
     def set_force_kernel(self, lanes=4):
-        """FP32 form: lanes per agent of the lane-per-agent kernel (1, 2, 4 =
-        default, 8, 16, 32; -1 = chosen per box by its cost model), or 0 for
-        the pair-ring kernel."""
+        """FP32 form: lanes per agent of the force kernel (1, 2, 4 = default,
+        8, 16, 32; -1 = chosen per box by its cost model)."""
         self._check(lib().bdm_set_force_kernel(self._h, int(lanes)))
 
     # ------------------------------------------------------------------ profiling

@@ -39,6 +39,7 @@ enum DevError : int32_t {
   DEV_ERANGE = 4,       // a simulation spans more than 2^21 boxes per axis
   DEV_EBOX = 5,         // more than BDM_MAX_BOX_AGENTS agents in one box
   DEV_ENONFINITE = 6,   // a position became non-finite
+  DEV_ECHECK = 7,       // a bounds check of the -DBDM_CHECK build failed (line in check_line)
 };
 
 #define BDM_MAX_BOX_AGENTS 65536
@@ -48,9 +49,12 @@ enum DevError : int32_t {
 #define FL_MOVED 2u    // position changed during the previous iteration
 #define FL_STATIC 4u   // skipped as static in the last iteration
 #define FL_DIVIDE 8u   // divides in the current iteration (scratch)
+#define FL_REMOVE 16u  // removed at the end of the current iteration (scratch)
 
 #define BEH_GROW 1u
 #define BEH_WALK 2u
+#define BEH_DIE 4u
+#define BEH_TYPE_SHIFT 4  // bits 4-5 of the behaviour byte: the agent's type
 
 struct AgentSet {
   double *x[2], *y[2], *z[2];
@@ -84,6 +88,8 @@ struct DevCounters {
   unsigned long long next_uid;
   int32_t error;
   int32_t history_valid;
+  int32_t check_line;   // -DBDM_CHECK build: source line of the first failed bounds check
+  int32_t pad_check;
   long long total_bricks, total_boxes, n_occ, n_div, max_brick;
   long long need_bricks, need_occ;
   int32_t sort_now, force_sort;
@@ -93,10 +99,17 @@ struct DevCounters {
   // (heavy list back), then the rest in Morton order
   unsigned long long heavy_n[2], heavy_take[2];
   unsigned long long work_n;     // entries of the static pass's work list
+  // removal (Sec. 3.2): agents removed this iteration, the size after the
+  // commit, the holes below it; ghosts = agents removed in the previous
+  // iteration, whose boxes the static test marks dirty
+  long long n_rm, rm_m;
+  unsigned long long rm_h;
+  long long n_ghost;
+  unsigned long long fix_n;      // FP32 form: agents listed for the FP64 fix-up pass
   // per-iteration accumulators (reset by the geometry kernel)
   unsigned long long a_static, a_moved, a_cand, a_nbr, a_contact, a_exact;
   // snapshot of the last completed iteration
-  unsigned long long l_static, l_moved, l_cand, l_nbr, l_contact, l_exact, l_div;
+  unsigned long long l_static, l_moved, l_cand, l_nbr, l_contact, l_exact, l_div, l_rm, l_fix;
   long long l_boxes, l_bricks, l_occ, l_max_brick;
 };
 
@@ -104,6 +117,8 @@ struct DevParams {
   double R, R2, L;
   double dt, dmax, k, gamma, adherence;
   double growth, divide_volume, ratio_lo, ratio_hi, walk_step;
+  double death_prob;                // per-iteration removal probability of BEH_DIE agents
+  uint64_t death_thr;               // ceil(death_prob * 2^53): the integer form of u < death_prob
   uint64_t seed;
   float Rf, R2_lo_f, R2_hi_f, Lf;   // FP32 prefilter: certain neighbour / certain not
   float cband1, cband2;             // contact band: W = cband1 * s + cband2 * s^2
@@ -111,13 +126,21 @@ struct DevParams {
   float box_eps;                    // relative error bound of the fast box path
   float graze;                      // FP32 overlaps below this (um) are "grazing"
   float graze_e;                    // error bound of an FP32 overlap (um)
+  float graze_exact;                // FP32 overlaps below this (um) are evaluated in FP64
   float rel_tol, abs_tol;           // FP32-form force tolerance the refinement keeps
+  float low_scale;                  // agents whose summed pair-force magnitude is below this
+                                    // are evaluated in FP64
+  float close2;                     // FP32 form, fix-up pass: pairs closer than this (um^2)
+                                    // are evaluated in FP64
+  float dir_e;                      // bound of the FP32 error of a coordinate difference
+                                    // (times sqrt 3): the direction error of a pair is dir_e / d
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   long long L_fix;                  // box edge in fixed point (multiple of 128)
-  int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk;
-  int32_t lanes_fixed;              // FP32 form: 0 = pair-ring kernel (k_force32); > 0 lanes
-                                    // per agent of the lane-per-agent kernel (k_force); -1 that
-                                    // kernel with lanes chosen per box by its cost model
+  int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk, die;
+  int32_t n_types;                  // > 1: the pair's constants are type_k / type_gamma[4 a + b]
+  double type_k[16], type_gamma[16];  // of the agents' types a, b (bits 4-5 of the behaviour)
+  int32_t lanes_fixed;              // FP32 form: > 0 lanes per agent of the force kernel; -1
+                                    // lanes chosen per box by its cost model
 };
 
 // Everything a kernel reaches, passed by value.
@@ -142,6 +165,10 @@ struct DevBufs {
   uint32_t *scan_a, *scan_b;      // block partials of the scans
   uint32_t *div_rank;
   dbl4 *stash;                 // daughter (x, y, z, volume) by mother index
+  dbl4 *ghost;                 // positions of the agents removed in the last iteration
+  uint4 *fix;                  // FP32 form: (sorted index, occupied brick * 64 + box, contacts,
+                               // neighbours) of the agents the FP64 fix-up pass evaluates
+  uint8_t *tp;                 // n_types > 1: the type of the agent at each sorted position
   double *fdbg;                   // 3 x cap forces (debug)
   int32_t *nbr_count;             // debug neighbour lists
   long long *nbr_off;
@@ -150,10 +177,26 @@ struct DevBufs {
   int32_t *heavy;                 // occ_cap: occupied indices of heavy bricks (both ends)
   unsigned long long *need;       // occ_cap: boxes with non-static agents (static pass)
   int32_t *worklist;              // occ_cap: light bricks with work left (static pass)
-  float4 *defer_c;                // FP32-form deferred pairs: contribution, bound
-  uint2 *defer_w;                 // FP32-form deferred pairs: index, agent | kind
   long long brick_cap, occ_cap, cap, nbr_cap;
 };
+
+// ----------------------------------------------------------------- bounds checks
+// The -DBDM_CHECK build evaluates BDM_IN(counters, condition) at every index
+// that a kernel derives from device data before it reads or writes through it
+// (box and brick indices, sorted positions, slots against capacities,
+// shared-memory tiles and queues).  A failed check sets the sticky error word
+// to DEV_ECHECK, records the source line, and the caller substitutes a safe
+// index or skips the access, so an out-of-range index becomes a reported
+// error instead of a fault.  The regular build compiles the checks away.
+#ifdef BDM_CHECK
+__device__ __forceinline__ bool bdm_check_in(DevCounters *C, bool ok, int line) {
+  if (!ok && atomicCAS(&C->error, 0, (int)DEV_ECHECK) == 0) C->check_line = line;
+  return ok;
+}
+#define BDM_IN(C, cond) bdm_check_in((C), (cond), __LINE__)
+#else
+#define BDM_IN(C, cond) true
+#endif
 
 // ----------------------------------------------------------------- helpers
 __device__ __forceinline__ unsigned long long enc_f64(double v) {
@@ -240,6 +283,35 @@ __device__ __forceinline__ int box_axis(double p, double lo, float lo_f, const D
   return (int)qd;
 }
 
+// ----------------------------------------------------------------- Philox
+// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
+// 64x64->128 products with the round multipliers; key bumped by the Weyl
+// constants between rounds.
+__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
+  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) { k0 += W0; k1 += W1; }
+    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
+    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
+    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+  }
+}
+
+#define PURPOSE_DEATH 3ull
+
+// Death of a BEH_DIE agent in iteration `step`: Philox4x64-10 with counter
+// (uid, step, PURPOSE_DEATH, 0) and key (seed, 0); the first word's top 53
+// bits give u in [0, 1), and the agent is removed iff u < death_prob, taken
+// exactly in integers as (w >> 11) < death_thr, death_thr = ceil(death_prob 2^53).
+__device__ __forceinline__ bool agent_dies(const DevParams &P, uint64_t uid, long long step) {
+  uint64_t c[4] = {uid, (uint64_t)step, PURPOSE_DEATH, 0ull};
+  philox4x64_10(c, P.seed, 0ull);
+  return (c[0] >> 11) < P.death_thr;
+}
+
 // ----------------------------------------------------------------- launchers
 struct LaunchCfg {
   int agent_blocks;   // grid-stride agent kernels
@@ -247,8 +319,7 @@ struct LaunchCfg {
   int scan_blocks;    // ceil(brick_cap / SCAN_TILE)
   int agent_scan_blocks;
   int occ_blocks;
-  int force_blocks;    // k_force (FP64 form, neighbour modes, fixed lanes per agent)
-  int force32_blocks;  // k_force32 (FP32 form)
+  int force_blocks;    // k_force
 };
 
 // default FP32 force kernel: the lane-per-agent kernel with 4 lanes per agent
@@ -259,11 +330,6 @@ struct LaunchCfg {
 #define FORCE_HEAVY_HI 1024
 #define FORCE_HEAVY_LO 256
 
-// the FP32 form's pair-ring force kernel: resident CTAs per SM, warps per
-// CTA, and capacity of each warp's deferred-pair list (global memory)
-constexpr int FORCE32_CTAS_PER_SM = 2;
-#define FORCE32_WARPS 8
-#define FORCE32_DCAP 512
 
 #define SCAN_TILE 2048
 #define SCAN_THREADS 256
@@ -279,6 +345,10 @@ void launch_brick_sort(const DevBufs &B, const DevParams &P, const LaunchCfg &c,
 void launch_gather(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
 void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s);
 void launch_divide(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
+int divide_launches(const DevParams &P);  // kernels launch_divide enqueues
+int force_launches(const DevParams &P);   // kernels launch_force enqueues (without the static pass)
+void launch_force_fix(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s);
+int force_fix_launches(const DevParams &P);
 void launch_finish(const DevBufs &B, const DevParams &P, cudaStream_t s);
 void launch_bbox(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s);
 void launch_debug_boxes(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int32_t *out_box,

@@ -19,7 +19,7 @@
 #include "bdm_internal.cuh"
 #include "bdm.h"
 
-#define BDM_ABI_VERSION 100
+#define BDM_ABI_VERSION 200
 
 namespace {
 thread_local std::string g_create_error = "no error";
@@ -64,10 +64,10 @@ struct bdm_sim {
 
 // phases of one iteration (bdm_phase_name)
 enum Phase { PH_GEOMETRY, PH_BRICK_RANK, PH_KEYS, PH_BRICK_SCAN, PH_SCATTER, PH_BRICK_SORT, PH_GATHER, PH_FORCE,
-             PH_DIVIDE, PH_FINISH, PH_COUNT };
+             PH_FORCE_FIX, PH_DIVIDE, PH_FINISH, PH_COUNT };
 static const char *kPhaseNames[PH_COUNT] = {"geometry", "brick_rank", "keys", "brick_scan", "scatter",
-                                            "brick_sort", "gather", "force", "divide", "finish"};
-static const int kPhaseLaunches[PH_COUNT] = {1, 1, 1, 3, 1, 2, 2, 2, 3, 1};
+                                            "brick_sort", "gather", "force", "force_fix", "divide", "finish"};
+static const int kPhaseLaunches[PH_COUNT] = {1, 1, 1, 3, 1, 2, 2, 2, 1, 3, 1};
 
 // ------------------------------------------------------------------ helpers
 static int fail(bdm_sim *s, int code, const std::string &msg) {
@@ -117,7 +117,6 @@ static void make_launch_cfg(bdm_sim *s) {
   s->lc.agent_scan_blocks = clampb((s->cap + SCAN_TILE - 1) / SCAN_TILE, 1, 1LL << 30);
   s->lc.occ_blocks = clampb(s->B.occ_cap, 1, sm * 4);
   s->lc.force_blocks = clampb(s->B.occ_cap, 1, sm * 4);
-  s->lc.force32_blocks = clampb(s->B.occ_cap, 1, sm * FORCE32_CTAS_PER_SM);
 }
 
 static int alloc_grid(bdm_sim *s, long long brick_cap, long long occ_cap) {
@@ -191,19 +190,25 @@ static int alloc_agents(bdm_sim *s) {
   A((void **)&B.c32, sizeof(float4) * cap);
   if (f64) A((void **)&B.c64, sizeof(dbl4) * cap);
   else B.c64 = nullptr;
-  if (!f64) {
-    // one deferred-pair list per warp of the FP32 force kernel's grid
-    const size_t nd = (size_t)s->sm_count * FORCE32_CTAS_PER_SM * FORCE32_WARPS * FORCE32_DCAP;
-    A((void **)&B.defer_c, sizeof(float4) * nd);
-    A((void **)&B.defer_w, sizeof(uint2) * nd);
-  } else {
-    B.defer_c = nullptr;
-    B.defer_w = nullptr;
-  }
   if (grow) {
     A((void **)&B.stash, sizeof(dbl4) * cap);
   } else {
     B.stash = nullptr;
+  }
+  if (s->dp.die) {
+    A((void **)&B.ghost, sizeof(dbl4) * cap);
+  } else {
+    B.ghost = nullptr;
+  }
+  if (!f64) {
+    A((void **)&B.fix, sizeof(uint4) * cap);
+  } else {
+    B.fix = nullptr;
+  }
+  if (s->dp.n_types > 1) {
+    A((void **)&B.tp, cap);
+  } else {
+    B.tp = nullptr;
   }
   if (s->P.keep_forces) A((void **)&B.fdbg, sizeof(double) * 3 * cap);
   if (rc) return rc;
@@ -251,14 +256,21 @@ static void enqueue_step(bdm_sim *s) {
   enqueue_grid(s);
   launch_gather(s->B, s->dp, s->lc, s->own);
   launch_force(s->B, s->dp, s->lc, FM_STEP, s->own);
-  if (s->dp.grow) launch_divide(s->B, s->dp, s->lc, s->own);
+  launch_force_fix(s->B, s->dp, s->lc, FM_STEP, s->own);
+  launch_divide(s->B, s->dp, s->lc, s->own);
   launch_finish(s->B, s->dp, s->own);
+}
+
+static int phase_launches(const bdm_sim *s, int p) {
+  if (p == PH_DIVIDE) return divide_launches(s->dp);
+  if (p == PH_FORCE) return force_launches(s->dp);
+  if (p == PH_FORCE_FIX) return force_fix_launches(s->dp);
+  return kPhaseLaunches[p];
 }
 
 static long long kernels_per_step(const bdm_sim *s) {
   long long k = 0;
-  for (int p = 0; p < PH_COUNT; ++p)
-    if (p != PH_DIVIDE || s->dp.grow) k += kPhaseLaunches[p];
+  for (int p = 0; p < PH_COUNT; ++p) k += phase_launches(s, p);
   if (s->dp.detect_static) k += 1;  // the static pass before the force kernel
   return k;
 }
@@ -280,7 +292,7 @@ static int prof_mark(bdm_sim *s, int phase) {
 static int enqueue_step_profiled(bdm_sim *s) {
   int rc;
   for (int p = 0; p < PH_COUNT; ++p) {
-    if (p == PH_DIVIDE && !s->dp.grow) continue;
+    if (phase_launches(s, p) == 0) continue;
     if ((rc = prof_mark(s, p))) return rc;
     switch (p) {
       case PH_GEOMETRY: launch_geometry(s->B, s->dp, s->own); break;
@@ -291,10 +303,11 @@ static int enqueue_step_profiled(bdm_sim *s) {
       case PH_BRICK_SORT: launch_brick_sort(s->B, s->dp, s->lc, s->own); break;
       case PH_GATHER: launch_gather(s->B, s->dp, s->lc, s->own); break;
       case PH_FORCE: launch_force(s->B, s->dp, s->lc, FM_STEP, s->own); break;
+      case PH_FORCE_FIX: launch_force_fix(s->B, s->dp, s->lc, FM_STEP, s->own); break;
       case PH_DIVIDE: launch_divide(s->B, s->dp, s->lc, s->own); break;
       default: launch_finish(s->B, s->dp, s->own); break;
     }
-    s->prof_launch[p] += kPhaseLaunches[p];
+    s->prof_launch[p] += phase_launches(s, p);
   }
   if ((rc = prof_mark(s, -1))) return rc;  // end of the iteration
   s->kernels += kernels_per_step(s);
@@ -335,6 +348,8 @@ static int handle_device_error(bdm_sim *s) {
   if (e == DEV_ECAP_AGENTS) return fail(s, BDM_ECAPACITY, "daughters would exceed the agent capacity");
   if (e == DEV_ERANGE) return fail(s, BDM_EINVAL, "a simulation spans more than 2^21 boxes along an axis");
   if (e == DEV_EBOX) return fail(s, BDM_EINVAL, "more than 65536 agents in one box");
+  if (e == DEV_ECHECK)
+    return fail(s, BDM_ECUDA, "device bounds check failed (source line " + std::to_string(h.check_line) + ")");
   return fail(s, BDM_EINVAL, "device error " + std::to_string(e));
 }
 
@@ -405,6 +420,17 @@ int bdm_create(const bdm_params *params, void *stream, bdm_sim **out) {
   if (!(P.dt >= 0.0) || !(P.max_displacement >= 0.0) || !(P.adherence >= 0.0) || !(P.walk_step >= 0.0))
     return fail(nullptr, BDM_EINVAL, "dt, max_displacement, adherence and walk_step must be >= 0");
   if (P.sort_every < 0) return fail(nullptr, BDM_EINVAL, "sort_every must be >= 0");
+  if (!(P.death_prob >= 0.0 && P.death_prob <= 1.0)) return fail(nullptr, BDM_EINVAL, "death_prob must be in [0, 1]");
+  if (P.death_prob > 0.0 && P.n_sims > 1) return fail(nullptr, BDM_EINVAL, "removal needs n_sims == 1");
+  if (P.n_types < 0 || P.n_types > 4) return fail(nullptr, BDM_EINVAL, "n_types must be in [0, 4]");
+  for (int a = 0; a < P.n_types && P.n_types > 1; ++a)
+    for (int b = 0; b < P.n_types; ++b) {
+      const double k = P.type_k[4 * a + b], g = P.type_gamma[4 * a + b];
+      if (!(std::isfinite(k) && std::isfinite(g) && k >= 0.0 && g >= 0.0))
+        return fail(nullptr, BDM_EINVAL, "type_k and type_gamma must be finite and >= 0");
+      if (k != P.type_k[4 * b + a] || g != P.type_gamma[4 * b + a])
+        return fail(nullptr, BDM_EINVAL, "type_k and type_gamma must be symmetric");
+    }
 
   bdm_sim *s = new bdm_sim();
   s->P = P;
@@ -697,6 +723,8 @@ int bdm_get_counters(bdm_sim *s, bdm_counters *out) {
   out->n_static = (int64_t)h.l_static;
   out->n_moved = (int64_t)h.l_moved;
   out->n_divided = (int64_t)h.l_div;
+  out->n_removed = (int64_t)h.l_rm;
+  out->n_fp64_fixup = (int64_t)h.l_fix;
   out->n_candidates = (int64_t)h.l_cand;
   out->n_neighbors = (int64_t)h.l_nbr;
   out->n_contacts = (int64_t)h.l_contact;
@@ -726,9 +754,9 @@ static int apply_params(bdm_sim *s, const bdm_params &P, int lanes) {
 
 int bdm_set_force_kernel(bdm_sim *s, int lanes) {
   if (!s) return BDM_EINVAL;
-  if (!(lanes == -1 || lanes == 0 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
+  if (!(lanes == -1 || lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 ||
         lanes == 32))
-    return fail(s, BDM_EINVAL, "lanes must be -1, 0, 1, 2, 4, 8, 16 or 32");
+    return fail(s, BDM_EINVAL, "lanes must be -1, 1, 2, 4, 8, 16 or 32");
   return apply_params(s, s->P, lanes);
 }
 
@@ -810,9 +838,9 @@ int bdm_autotune(bdm_sim *s, int trial_steps, int what, bdm_tuning *out) {
       }
     }
     if (rc == BDM_OK && (what & BDM_TUNE_LANES) && base.precision == BDM_FP32_FORCE) {
-      const int opts[5] = {FORCE_LANES_DEFAULT, 0, -1, 2, 8};
+      const int opts[4] = {FORCE_LANES_DEFAULT, -1, 2, 8};
       int bl = best_lanes;
-      for (int i = 0; i < 5 && rc == BDM_OK; ++i)
+      for (int i = 0; i < 4 && rc == BDM_OK; ++i)
         if ((rc = trial(best, opts[i], &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; bl = opts[i]; }
       best_lanes = bl;
     }

@@ -23,23 +23,6 @@
 
 namespace {
 
-// ---------------------------------------------------------------- Philox
-// Philox4x64-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds of two
-// 64x64->128 products with the round multipliers; key bumped by the Weyl
-// constants between rounds.
-__device__ __forceinline__ void philox4x64_10(uint64_t c[4], uint64_t k0, uint64_t k1) {
-  const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-  const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) { k0 += W0; k1 += W1; }
-    const uint64_t hi0 = __umul64hi(M0, c[0]), lo0 = M0 * c[0];
-    const uint64_t hi1 = __umul64hi(M1, c[2]), lo1 = M1 * c[2];
-    const uint64_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
-    c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
-  }
-}
-
 #define PURPOSE_RATIO 0ull
 #define PURPOSE_AXIS 1ull
 #define PURPOSE_WALK 2ull
@@ -180,15 +163,11 @@ __device__ __forceinline__ int pair_f64_k(double R2, double k, double gamma, con
   fz = __dadd_rn(fz, __dmul_rn(sc, ddz));
   return 2;
 }
-__device__ __forceinline__ int pair_f64(const DevParams &P, const dbl4 &q, const dbl4 &c, double &fx, double &fy,
-                                        double &fz) {
-  return pair_f64_k(P.R2, P.k, P.gamma, q, c, fx, fy, fz);
-}
-// The same pair as pair_f64, returning the three products sc * (q - c) that
-// pair_f64 adds to the running sum (so a caller can add them later, in the
+// The same pair as pair_f64_k, returning the three products sc * (q - c) that
+// pair_f64_k adds to the running sum (so a caller can add them later, in the
 // same order, with the same IEEE operations).
-__device__ __forceinline__ int pair_f64_terms(const DevParams &P, const dbl4 &q, const dbl4 &c, double &tx, double &ty,
-                                              double &tz) {
+__device__ __forceinline__ int pair_f64_terms(const DevParams &P, double k, double gamma, const dbl4 &q, const dbl4 &c,
+                                              double &tx, double &ty, double &tz) {
   const double ddx = __dsub_rn(q.x, c.x), ddy = __dsub_rn(q.y, c.y), ddz = __dsub_rn(q.z, c.z);
   const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(ddx, ddx), __dmul_rn(ddy, ddy)), __dmul_rn(ddz, ddz));
   if (!(d2 < P.R2)) return 0;
@@ -197,7 +176,7 @@ __device__ __forceinline__ int pair_f64_terms(const DevParams &P, const dbl4 &q,
   const double delta = __dsub_rn(__dadd_rn(q.w, c.w), d);
   if (!(delta > 0.0)) return 1;
   const double rbar = __ddiv_rn(__dmul_rn(q.w, c.w), __dadd_rn(q.w, c.w));
-  const double F = __dsub_rn(__dmul_rn(P.k, delta), __dmul_rn(P.gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
+  const double F = __dsub_rn(__dmul_rn(k, delta), __dmul_rn(gamma, __dsqrt_rn(__dmul_rn(rbar, delta))));
   const double sc = __ddiv_rn(F, d);
   tx = __dmul_rn(sc, ddx);
   ty = __dmul_rn(sc, ddy);
@@ -243,6 +222,7 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 
 #define FORCE_WARPS 8
 #define CHUNK 96
+#define RISK_SLOTS 2  // risky contacts a lane records for the FP64 replay
 
 // Next occupied brick for a force-kernel CTA (called by one thread; phase is
 // that thread's cursor, starting at 0): the heaviest bricks first, so that no
@@ -332,7 +312,14 @@ __device__ __forceinline__ void finish_agent(const DevBufs &B, const DevParams &
     c_static++;
     Fx = Fy = Fz = 0.0;
   } else {
-    const uint8_t beh = (P.walk || P.grow) ? A.beh[iq] : (uint8_t)0;
+    const uint8_t beh = (P.walk || P.grow || P.die) ? A.beh[iq] : (uint8_t)0;
+    if (P.die && (beh & BEH_DIE) && agent_dies(P, A.uid[iq], step)) {
+      // removed at the end of this iteration (Sec. 3.2): no displacement,
+      // growth or division, and no part in the next grid's bounding box
+      A.flags[iq] = FL_REMOVE;
+      A.nz[iq] = (uint16_t)min(ncont, 65535u);
+      return;
+    }
     if (PREC == 1) {
       float ux, uy, uz;
       displacement_f32(P, dt_f, ffx, ffy, ffz, ux, uy, uz);
@@ -461,6 +448,65 @@ __device__ __forceinline__ unsigned scan_chunk(const float4 *sc, uint8_t *q, con
   return (unsigned)(q - q0) >> 5;
 }
 
+// FP32 force of a certain contact at squared distance d2 (s = r_i + r_j, pi =
+// r_i r_j): overlap delta, the scale F / d of the difference vector, and the
+// force F itself.  Every operation is rounded as written (the fused
+// multiply-adds are explicit), so the force kernel and the FP64 replay form
+// the same bits.
+struct ContactF32 {
+  float inv_d, delta, rbar, sq, fm, scf;
+};
+__device__ __forceinline__ ContactF32 contact_f32(float d2, float s, float pi, float k, float gamma) {
+  ContactF32 c;
+  c.inv_d = rsqrtf(d2);
+  c.delta = fmaf(-d2, c.inv_d, s);
+  c.rbar = __fdividef(pi, s);
+  const float rd = __fmul_rn(c.rbar, c.delta);  // > 0 for a certain contact
+  c.sq = __fmul_rn(rd, rsqrtf(rd));
+  c.fm = fmaf(k, c.delta, -__fmul_rn(gamma, c.sq));
+  c.scf = __fmul_rn(c.fm, c.inv_d);
+  return c;
+}
+
+// FP64 replay of a lane's recorded risky contacts (FP32 form): for each, the
+// FP64 contribution minus the FP32 contribution the force kernel added for it
+// (recomputed with the same FP32 operations from the same staged record:
+// box-local coordinates plus the offset of its stencil box, found among the
+// warp's 27 box ranges pre/st), summed into d*.  Out of line, so that the
+// force kernel's main loop keeps its registers.
+__device__ __noinline__ void replay_risky(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, unsigned kq,
+                                          float4 cq, int tq4, unsigned nrisk, const uint32_t *rk, const unsigned *pre,
+                                          const unsigned *st, const float4 *off, const double *tkd, const double *tgd,
+                                          const float *tkf, const float *tgf, float &dx, float &dy, float &dz,
+                                          unsigned &n_exact) {
+  const dbl4 pq = exact_of<1>(B, A, cur, kq);
+  double hx = 0.0, hy = 0.0, hz = 0.0;
+  float fx = 0.f, fy = 0.f, fz = 0.f;
+  for (unsigned r = 0; r < nrisk; ++r) {
+    const unsigned kj = rk[32 * r];
+    int bx = 0;
+    for (int b = 0; b < 27; ++b)
+      if (kj - st[b] < pre[b + 1] - pre[b]) bx = b;  // kj in box b's range (unsigned wrap excludes below)
+    const float4 of = off[bx];
+    const float4 c0 = B.c32[kj];
+    const float4 c = make_float4(c0.x + of.x, c0.y + of.y, c0.z + of.z, c0.w);
+    const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
+    // the force kernel's FP32 contribution of this (certain, FP32) contact
+    const float2 e = sub_xy(cq, c);
+    const float ez = cq.z - c.z;
+    const float d2 = fmaf(e.x, e.x, fmaf(e.y, e.y, __fmul_rn(ez, ez)));
+    const ContactF32 k = contact_f32(d2, __fadd_rn(cq.w, c.w), __fmul_rn(cq.w, c.w), tkf[ab], tgf[ab]);
+    fx = fmaf(k.scf, e.x, fx);
+    fy = fmaf(k.scf, e.y, fy);
+    fz = fmaf(k.scf, ez, fz);
+    atomicAdd(&n_exact, 1u);
+    pair_f64_k(P.R2, tkd[ab], tgd[ab], pq, exact_of<1>(B, A, cur, kj), hx, hy, hz);
+  }
+  dx = (float)(hx - (double)fx);
+  dy = (float)(hy - (double)fy);
+  dz = (float)(hz - (double)fz);
+}
+
 // SPLIT (FP32 step without random walk or growth only): the agent's lanes
 // finish one axis each.  A separate instantiation, so that the other forms
 // keep the register allocation they have without that code.
@@ -487,6 +533,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ uint32_t s_kj[FORCE_WARPS][CHUNK];
   __shared__ uint8_t s_q[FORCE_WARPS][CHUNK][32];
   __shared__ unsigned s_pre[FORCE_WARPS][28], s_st[FORCE_WARPS][28];
+  // several agent types: the staged candidates' types and the pair constants
+  __shared__ uint8_t s_tp[FORCE_WARPS][CHUNK];
+  // FP32 form: per lane, the sorted indices of its first risky contacts
+  __shared__ uint32_t s_rk[FORCE_WARPS][RISK_SLOTS][32];
+  __shared__ float s_tkf[16], s_tgf[16];
+  __shared__ double s_tkd[16], s_tgd[16];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
@@ -504,6 +556,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   }
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
   if (lane < 4) s_ctr[warp][lane] = 0u;
+  if (threadIdx.x < 16) {
+    s_tkd[threadIdx.x] = P.type_k[threadIdx.x];
+    s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
+    s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
+    s_tgf[threadIdx.x] = (float)P.type_gamma[threadIdx.x];
+  }
 
   // One block per occupied brick (taken from a global counter); its warps
   // take the brick's 64 boxes from a block counter.
@@ -514,8 +572,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       s_next = 0;
     }
     __syncthreads();
-    const long long o = s_o;
+    long long o = s_o;
     if (o < 0) break;
+    if (!BDM_IN(B.ctr, o < n_occ)) break;  // block-uniform
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
     if (threadIdx.x < 27) {
@@ -587,10 +646,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         if (lane >= of) pre += y;
       }
       const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
-      if (lane < 27) {
-        s_pre[warp][lane] = pre - nb_cnt;
-        s_st[warp][lane] = nb_st;
-      }
+      if (lane <= 27) s_pre[warp][lane] = pre - nb_cnt;  // s_pre[27] = ctot
+      if (lane < 27) s_st[warp][lane] = nb_st;
       __syncwarp();
       // lanes per agent: split the candidates of small boxes over several lanes
       int S = 1;
@@ -608,14 +665,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       const unsigned G_ = 32u / S;
       for (unsigned q0 = 0; q0 < nq; q0 += G_) {
         const unsigned qi = q0 + (unsigned)(lane / S);
-        const bool valid = qi < nq;
-        const unsigned kq = qbase + (valid ? qi : 0u);
-        const uint32_t iq = B.perm[kq];
+        bool valid = qi < nq;
+        unsigned kq = qbase + (valid ? qi : 0u);
+        if (!BDM_IN(B.ctr, (long long)kq < C->n)) { kq = 0; valid = false; }
+        uint32_t iq = B.perm[kq];
+        if (!BDM_IN(B.ctr, (long long)iq < B.cap)) { iq = 0; valid = false; }
         const float4 cq = B.c32[kq];
         dbl4 dq = mk_dbl4(0.0, 0.0, 0.0, 0.0);
         if (PREC == 0) dq = B.c64[kq];
         const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
         const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+        const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;  // the agent's row of the type tables
         if (SPLIT && S >= 4 && valid && !is_static && sub < 3) {
           // this lane's axis of the agent's position, copied to shared memory
           // while the pairs are evaluated (waited for in the epilogue)
@@ -630,17 +690,14 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           const unsigned na = __popc(__ballot_sync(0xffffffffu, compute));
           if (lane == 0) s_ctr[warp][0] += ctot * (na / (unsigned)S);
         }
-        float ffx = 0.f, ffy = 0.f, ffz = 0.f;
-        float gfx = 0.f, gfy = 0.f, gfz = 0.f, gbound = 0.f, fscale = 0.f;
+        float ffx = 0.f, ffy = 0.f, ffz = 0.f, gbound = 0.f, fscale = 0.f;
+        unsigned nrisk = 0;  // FP32 form: risky contacts (the first ones' indices in s_rk)
         double dfx = 0.0, dfy = 0.0, dfz = 0.0;
         unsigned ncont = 0, nnb = 0;
         long long lbase = 0;
         if (MODE == FM_LIST_NBR && valid) lbase = B.nbr_off[iq];
-        bool refine = false;
-        double hx = 0.0, hy = 0.0, hz = 0.0;
-        for (int pass = 0; pass < 2; ++pass) {
-          const bool act = (pass == 0) ? compute : refine;
-          if (__any_sync(0xffffffffu, act)) {
+        {
+          if (__any_sync(0xffffffffu, compute)) {
             // The warp stages its stencil's candidates in chunks of CHUNK
             // records in shared memory (coalesced copies, neighbour-box offset
             // applied once), every lane tests its share of the chunk in FP32
@@ -671,6 +728,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   if (lo + step <= 26 && s_pre[warp][lo + step] <= p) lo += step;
                 boxs[m] = lo;
                 kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
+                if (!BDM_IN(B.ctr, p >= ctot || (long long)kjs[m] < C->n)) kjs[m] = 0;
               }
               float4 cs[PER_LANE];
 #pragma unroll
@@ -683,6 +741,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   const float4 of = s_off[boxs[m]];
                   sc[t] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
                   skj[t] = kjs[m];
+                  if (P.n_types > 1) s_tp[warp][t] = B.tp[kjs[m]];
                 }
               }
               c0 += fill;
@@ -690,7 +749,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
               __syncwarp();
               // ---- test the chunk in FP32, queue the candidates inside the band
               unsigned qlen = 0;
-              if (act) {
+              if (compute) {
                 // the default stride (4 lanes per agent) with constant offsets
                 qlen = (S == 4) ? scan_chunk<4>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, 4u, fill, P.R2_hi_f)
                                 : scan_chunk<0>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, (unsigned)S, fill,
@@ -729,7 +788,13 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                       if (ow + st < 32 && qs[ow + st] <= e) ow += st;
                     const unsigned kj = skj[s_q[warp][e - qs[ow]][ow]];
                     const unsigned ko = kqs[ow];
-                    if (kj != ko) r = pair_f64_terms(P, B.c64[ko], B.c64[kj], tx, ty, tz);
+                    double kk = P.k, gg = P.gamma;
+                    if (P.n_types > 1) {
+                      const int ab = 4 * (int)B.tp[ko] + (int)B.tp[kj];
+                      kk = s_tkd[ab];
+                      gg = s_tgd[ab];
+                    }
+                    if (kj != ko) r = pair_f64_terms(P, kk, gg, B.c64[ko], B.c64[kj], tx, ty, tz);
                   }
                   __syncwarp();
                   tr[lane] = tx;
@@ -768,14 +833,15 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                     }
                     continue;
                   }
-                  const int r = pair_f64(P, dq, cj, dfx, dfy, dfz);
+                  const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
+                  const int r = pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, cj, dfx, dfy, dfz);
                   nnb += (r > 0);
                   ncont += (r == 2);
                   continue;
                 }
                 const float4 c = sc[i];
-                const float ex = cq.x - c.x, ey = cq.y - c.y, ez = cq.z - c.z;
-                const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+                const float ex = __fsub_rn(cq.x, c.x), ey = __fsub_rn(cq.y, c.y), ez = __fsub_rn(cq.z, c.z);
+                const float d2 = fmaf(ex, ex, fmaf(ey, ey, __fmul_rn(ez, ez)));
                 const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
                   bool isn = true;
@@ -789,68 +855,60 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   }
                   continue;
                 }
-                const float s = cq.w + c.w, s2 = s * s;
+                const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
                 const float W = fmaf(s, P.cband1, s2 * P.cband2);
-                if (pass == 1 && (band || d2 > s2 - W)) continue;  // not an FP32 contact
-                if (band || (d2 > s2 - W && d2 < s2 + W)) {
-                  // cutoff or contact decided in FP64
+                const int ab = tq4 + ((P.n_types > 1) ? (int)s_tp[warp][i] : 0);
+                bool exact = band || (d2 > s2 - W && d2 < s2 + W);  // cutoff or contact decided in FP64
+                ContactF32 k = {};
+                if (!exact) {
+                  if (d2 >= s2 + W) {  // a neighbour, certainly no contact
+                    nnb++;
+                    continue;
+                  }
+                  k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
+                  // a contact so shallow that gamma sqrt(rbar delta) is too steep
+                  // for the FP32 overlap: in FP64 as well
+                  exact = k.delta < P.graze_exact;
+                }
+                if (exact) {
                   atomicAdd(&s_ctr[warp][3], 1u);
                   double gx = 0.0, gy = 0.0, gz = 0.0;
-                  const int r = pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                  const int r = pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], exact_of<1>(B, A, cur, kq),
+                                           exact_of<1>(B, A, cur, kj), gx, gy, gz);
                   nnb += (r > 0);
                   if (r == 2) {
                     ncont++;
-                    ffx += (float)gx; ffy += (float)gy; ffz += (float)gz;
+                    const float tx = (float)gx, ty = (float)gy, tz = (float)gz;
+                    ffx += tx; ffy += ty; ffz += tz;
+                    fscale += sqrtf(fmaf(tx, tx, fmaf(ty, ty, tz * tz)));
                   }
                   continue;
                 }
-                if (pass == 0) nnb++;
-                if (d2 >= s2 + W) continue;  // certainly no contact
-                const float inv_d = rsqrtf(d2);
-                const float d = d2 * inv_d;
-                const float delta = s - d;
-                const float rbar = __fdividef(cq.w * c.w, s);
-                const float rd = rbar * delta;            // > 0: a certain contact
-                const float sq = rd * rsqrtf(rd);
-                const float kd = P.kf * delta, gs = P.gammaf * sq;
-                const float scf = (kd - gs) * inv_d;
-                if (pass == 1) {
-                  // refinement: the grazing contacts of pass 0, classified by the
-                  // same FP32 arithmetic, redone in FP64
-                  if (delta < P.graze) {
-                    atomicAdd(&s_ctr[warp][3], 1u);
-                    pair_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), hx, hy, hz);
-                  }
-                  continue;
+                nnb++;
+                const float gf = s_tgf[ab], delta = k.delta, rbar = k.rbar, sq = k.sq, fm = k.fm, scf = k.scf;
+                // a contact whose FP32 error is not negligible against a small
+                // tolerance (grazing, near the sign change of the force, or a
+                // close pair): summed apart, its index kept for an FP64 replay
+                if (delta < P.graze || fabsf(fm) < P.low_scale || d2 < P.close2) {
+                  if (nrisk < RISK_SLOTS) s_rk[warp][nrisk][lane] = kj;
+                  nrisk++;
                 }
-                if (delta < P.graze) {
-                  // grazing contact: d/d(delta) of sqrt(rbar delta) is large,
-                  // so keep it apart with a bound of its FP32 error
-                  gfx = fmaf(scf, ex, gfx);
-                  gfy = fmaf(scf, ey, gfy);
-                  gfz = fmaf(scf, ez, gfz);
-                  gbound += (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
-                                                  P.gammaf * sqrtf(rbar * P.graze_e))
-                                          : P.gammaf * sqrtf(rbar * P.graze_e);
-                } else {
-                  ffx = fmaf(scf, ex, ffx);
-                  ffy = fmaf(scf, ey, ffy);
-                  ffz = fmaf(scf, ez, ffz);
-                }
-                fscale += kd + gs;
+                ffx = fmaf(scf, ex, ffx);
+                ffy = fmaf(scf, ey, ffy);
+                ffz = fmaf(scf, ez, ffz);
+                // error bound: the direction (p_i - p_j) / d carries the
+                // coordinates' rounding over d (large for close pairs), and
+                // a grazing contact's sqrt(rbar delta) is steep in delta
+                gbound = fmaf(fabsf(scf), P.dir_e, gbound);
+                if (delta < P.graze)
+                  gbound += (sq > 1e-18f) ? fminf(gf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
+                                                  gf * sqrtf(rbar * P.graze_e))
+                                          : gf * sqrtf(rbar * P.graze_e);
+                fscale += fabsf(fm);
                 ncont++;
               }
               __syncwarp();
             }
-          }
-          if (pass == 1) {
-            for (int of = S >> 1; of > 0; of >>= 1) {
-              hx += __shfl_xor_sync(0xffffffffu, hx, of);
-              hy += __shfl_xor_sync(0xffffffffu, hy, of);
-              hz += __shfl_xor_sync(0xffffffffu, hz, of);
-            }
-            if (refine) { gfx = (float)hx; gfy = (float)hy; gfz = (float)hz; }
-            break;
           }
           // reduce the S partial sums of an agent
           for (int of = S >> 1; of > 0; of >>= 1) {
@@ -860,23 +918,45 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
             ncont += __shfl_xor_sync(0xffffffffu, ncont, of);
             nnb += __shfl_xor_sync(0xffffffffu, nnb, of);
             if (PREC == 1) {
-              gfx += __shfl_xor_sync(0xffffffffu, gfx, of);
-              gfy += __shfl_xor_sync(0xffffffffu, gfy, of);
-              gfz += __shfl_xor_sync(0xffffffffu, gfz, of);
               gbound += __shfl_xor_sync(0xffffffffu, gbound, of);
               fscale += __shfl_xor_sync(0xffffffffu, fscale, of);
             }
           }
-          if (PREC != 1 || !(MODE == FM_STEP || MODE == FM_FORCES)) break;
-          // accept the grazing sum when its error bound is a small part of the
-          // agent's tolerance; otherwise redo those pairs in FP64 (pass 1)
-          refine = compute && gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol);
-          if (!__any_sync(0xffffffffu, refine)) break;
         }
+        // FP32 form: the agent's tolerance is rel_tol * S + abs_tol, S =
+        // fscale, the sum of its pair-force magnitudes.  When the FP32 error
+        // bound is not a small part of it, or S is so small that the absolute
+        // floor dominates (S < low_scale: the coordinates' rounding, about
+        // 1e-6 um per contact, is no longer negligible), the agent's risky
+        // contacts are replayed in FP64 here (their FP32 sum replaced), or,
+        // when a lane had more of them than it could record, the agent goes to
+        // the FP64 fix-up pass, which evaluates and finishes it.
+        bool need_fix = false;
         if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
-          ffx += gfx;
-          ffy += gfy;
-          ffz += gfz;
+          const bool flagged = compute && ncont > 0 &&
+                               (fscale < P.low_scale || gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol));
+          unsigned over = (nrisk > RISK_SLOTS) ? 1u : 0u;
+          for (int of = S >> 1; of > 0; of >>= 1) over |= __shfl_xor_sync(0xffffffffu, over, of);
+          const bool replay = flagged && !over;
+          need_fix = flagged && over;
+          if (__any_sync(0xffffffffu, replay)) {
+            // each lane: sum over its recorded contacts of (FP64 contribution
+            // - the FP32 contribution it added above, recomputed by the same
+            // arithmetic), so that the FP64 values replace the FP32 ones
+            float dx = 0.f, dy = 0.f, dz = 0.f;
+            if (replay) replay_risky(B, P, A, cur, kq, cq, tq4, nrisk, &s_rk[warp][0][lane], s_pre[warp], s_st[warp],
+                                     s_off, s_tkd, s_tgd, s_tkf, s_tgf, dx, dy, dz, s_ctr[warp][3]);
+            for (int of = S >> 1; of > 0; of >>= 1) {
+              dx += __shfl_xor_sync(0xffffffffu, dx, of);
+              dy += __shfl_xor_sync(0xffffffffu, dy, of);
+              dz += __shfl_xor_sync(0xffffffffu, dz, of);
+            }
+            if (replay) { ffx += dx; ffy += dy; ffz += dz; }
+          }
+          if (need_fix && sub == 0) {
+            const unsigned long long e = atomicAdd(&C->fix_n, 1ull);
+            if (BDM_IN(B.ctr, (long long)e < B.cap)) B.fix[e] = make_uint4(kq, (uint32_t)(o * 64 + lb), ncont, nnb);
+          }
         }
         if (SPLIT && S >= 4) {
           // Lanes 0, 1 and 2 of the agent finish one axis each (one FP64
@@ -884,10 +964,10 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           // with the same arithmetic as finish_agent's FP32 form.
           float ux, uy, uz;
           displacement_f32(P, dt_f, ffx, ffy, ffz, ux, uy, uz);
-          const bool live = valid && !is_static && sub < 3;
+          if (valid && !is_static && sub < 3) asm volatile("cp.async.wait_all;\n" ::: "memory");
+          const bool live = valid && !is_static && !need_fix && sub < 3;
           double p = 0.0, np = 0.0;
           if (live) {
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
             p = s_pos[warp][lane];
             const float u = (sub == 0) ? ux : (sub == 1) ? uy : uz;
             np = (u != 0.f) ? __dadd_rn(p, ftod_exact(u)) : p;
@@ -918,6 +998,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         if (MODE == FM_COUNT_NBR) { B.nbr_count[iq] = (int32_t)nnb; continue; }
         if (MODE == FM_LIST_NBR) continue;
         if (is_static) continue;  // finished by the static pass
+        if (need_fix) continue;   // finished by the FP64 fix-up pass
         double px = 0.0, py = 0.0, pz = 0.0;
         if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
         finish_agent<PREC, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, ffx, ffy, ffz, dfx, dfy, dfz,
@@ -937,80 +1018,6 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
     if (t_cont) atomicAdd(&C->a_contact, t_cont);
     if (t_exact) atomicAdd(&C->a_exact, t_exact);
   }
-}
-
-// Exact FP64 inputs of a pair, for the out-of-line settle step of k_force32.
-struct ExactSrc {
-  const uint32_t *perm;
-  const double *x, *y, *z;
-  const float4 *c32;
-  double R2, k, gamma;
-};
-
-// Settle the deferred pairs of a k_force32 warp (called by the whole warp).
-// Entry e holds the candidate's sorted index and the agent slot and kind in
-// dw[e], and for a grazing pair its FP32 contribution and error bound in
-// dc[e].  Band pairs are evaluated in FP64 and added with their neighbour and
-// contact counts; the grazing pairs of agents in rmask are redone in FP64,
-// replacing their FP32 contribution and removing their bound.  Each agent's
-// owner lane adds its settled pairs in list order.  kq0 is the sorted index of
-// agent slot 0.  Returns this lane's count of FP64 pair evaluations.
-#define DA_EXACT 0x100u
-#define DA_NBR 0x200u
-#define DA_CONT 0x400u
-__device__ __noinline__ unsigned settle_deferred(ExactSrc X, unsigned kq0, unsigned dlen, unsigned rmask, float4 *dc,
-                                                 uint2 *dw, float4 *acc, float *bnd, uint32_t *nnb_s,
-                                                 uint32_t *nct_s) {
-  const unsigned lane = threadIdx.x & 31;
-  unsigned n_exact = 0;
-  for (unsigned e0 = 0; e0 < dlen; e0 += 32) {
-    const unsigned e = e0 + lane;
-    bool need = false;
-    if (e < dlen) {
-      const uint2 w = dw[e];
-      const unsigned a = w.y & 0xffu;
-      const bool ex = (w.y & DA_EXACT) != 0;
-      need = ex || ((rmask >> a) & 1u);
-      if (need) {
-        n_exact++;
-        const unsigned kq = kq0 + a, kj = w.x;
-        const uint32_t iq = X.perm[kq], ij = X.perm[kj];
-        const dbl4 pq = mk_dbl4(X.x[iq], X.y[iq], X.z[iq], ftod_exact(X.c32[kq].w));
-        const dbl4 pj = mk_dbl4(X.x[ij], X.y[ij], X.z[ij], ftod_exact(X.c32[kj].w));
-        double gx = 0.0, gy = 0.0, gz = 0.0;
-        const int r = pair_f64_k(X.R2, X.k, X.gamma, pq, pj, gx, gy, gz);
-        if (ex) {
-          dc[e] = make_float4((float)gx, (float)gy, (float)gz, 0.f);
-          dw[e].y = w.y | (r > 0 ? DA_NBR : 0u) | (r == 2 ? DA_CONT : 0u);
-        } else {
-          // FP64 contribution in place of the FP32 one; its bound goes
-          const float4 d = dc[e];
-          dc[e] = make_float4((float)gx - d.x, (float)gy - d.y, (float)gz - d.z, d.w);
-        }
-      }
-    }
-    unsigned nm = __ballot_sync(0xffffffffu, need);
-    __syncwarp();
-    for (; nm; nm &= nm - 1) {
-      const unsigned e1 = e0 + (unsigned)(__ffs(nm) - 1);
-      const unsigned w = dw[e1].y;
-      if (lane == (w & 0xffu)) {
-        const float4 d = dc[e1];
-        float4 t = acc[lane];
-        t.x += d.x; t.y += d.y; t.z += d.z;
-        acc[lane] = t;
-        if (w & DA_EXACT) {
-          nnb_s[lane] += (w & DA_NBR) ? 1u : 0u;
-          nct_s[lane] += (w & DA_CONT) ? 1u : 0u;
-        } else {
-          bnd[lane] -= d.w;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  __syncwarp();
-  return n_exact;
 }
 
 // ---------------------------------------------------------------- static pass
@@ -1095,6 +1102,12 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P
         atomicAdd(&s_work[w][lb], 1u);
         continue;
       }
+      if (P.die && (A.beh[iq] & BEH_DIE) && agent_dies(P, A.uid[iq], C->step)) {
+        A.flags[iq] = FL_STATIC | FL_REMOVE;  // removed at the end of the iteration
+        if (P.keep_forces) { B.fdbg[iq] = 0.0; B.fdbg[B.cap + iq] = 0.0; B.fdbg[2 * B.cap + iq] = 0.0; }
+        c_static++;
+        continue;
+      }
       if (fl != FL_STATIC) A.flags[iq] = FL_STATIC;
       const unsigned long long e[3] = {enc_f64(A.x[cur][iq]), enc_f64(A.y[cur][iq]), enc_f64(A.z[cur][iq])};
       for (int d = 0; d < 3; ++d) { mn[d] = min(mn[d], e[d]); mx[d] = max(mx[d], e[d]); }
@@ -1106,7 +1119,10 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P
                                     ((unsigned long long)__ballot_sync(0xffffffffu, s_work[w][lane + 32] > 0u) << 32);
     if (lane == 0) {
       B.need[o] = need;
-      if (need && m < FORCE_HEAVY_LO) B.worklist[atomicAdd(&C->work_n, 1ull)] = (int32_t)o;
+      if (need && m < FORCE_HEAVY_LO) {
+        const unsigned long long e = atomicAdd(&C->work_n, 1ull);
+        if (BDM_IN(B.ctr, (long long)e < B.occ_cap)) B.worklist[e] = (int32_t)o;
+      }
     }
     __syncwarp();
   }
@@ -1115,420 +1131,194 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P
   if (lane == 0 && t) atomicAdd(&C->a_static, t);
 }
 
-// ---------------------------------------------------------------- FP32 form: pair-ring kernel
-// The FP32 form's production kernel.  Same work decomposition as k_force
-// (one CTA per occupied brick, one warp per box), but the pairs are not
-// evaluated lane-per-agent.  For a group of up to 32 agents of a box the warp
-// stages the stencil's candidates in shared memory (up to F32_CHUNK at a
-// time; most stencils fit at once); for every agent it tests 32 candidates
-// per instruction in FP32 and appends the (agent, candidate) indices of those
-// inside the cutoff band to a ring (ballot + popcount positions).  Whenever
-// the ring holds 32 pairs they are evaluated with every lane busy, and a
-// segmented shuffle reduction over the agent index folds them into per-agent
-// sums in shared memory.  Pairs that FP32 cannot decide (cutoff or contact
-// band) and grazing contacts are also written to the warp's deferred list in
-// global memory, settled in FP64 at the end of the group: band pairs always,
-// grazing pairs when the agent's summed FP32 error bound is not a small part
-// of its tolerance (their FP32 contribution is then replaced).
-#define F32_WARPS FORCE32_WARPS
-#define F32_MINB FORCE32_CTAS_PER_SM
-#define F32_CHUNK 448
-#define F32_RING 512
-#define F32_DCAP FORCE32_DCAP
-// per warp: staged chunk (float4 + index), the ring, the group's agents,
-// their sums (float4 each) and positions (three doubles), bounds and the two
-// counts (one word each)
-#define F32_WARP_SMEM (F32_CHUNK * 20 + F32_RING * 4 + 32 * 16 * 2 + 32 * 8 * 3 + 32 * 4 * 3)
+__global__ void k_reset_work(DevBufs B) {
+  B.ctr->work_next = 0;
+  B.ctr->heavy_take[0] = B.ctr->heavy_take[1] = 0;
+  B.ctr->fix_n = 0;
+}
 
+// ---------------------------------------------------------------- FP64 fix-up (FP32 form)
+// The FP32-form agents that the force kernel listed (an FP32 error bound not
+// small against the agent's tolerance, or a summed pair-force magnitude so
+// small that the absolute floor dominates) are evaluated again here, one warp
+// per agent: the lanes take strides of the agent's 27-box stencil.  Every
+// contact the FP32 error analysis does not cover -- one the FP32 bands cannot
+// decide, a grazing contact (delta < graze), a contact whose force magnitude
+// is below low_scale (near the sign change of k delta - gamma sqrt(rbar
+// delta), where rounding is large against the force) and a close pair
+// (d^2 < close2, whose direction carries the coordinates' rounding over d) --
+// is evaluated in FP64; the other contacts exactly as the force kernel does.
+// The sum, rounded to FP32, goes through the force kernel's epilogue
+// (displacement, behaviours, flags, bounding box), or to the debug outputs in
+// FM_FORCES; the neighbour and contact counts are the force kernel's.
+#define FIX_WARPS 8
+#define FIX_BATCH 4
 template <int MODE>
-__global__ void __launch_bounds__(F32_WARPS * 32, F32_MINB) k_force32(DevBufs B, DevParams P) {
-  __shared__ int s_nocc[27];
-  __shared__ unsigned long long s_ndirty[27];
-  __shared__ int s_next;
-  __shared__ unsigned s_bcnt[64];
-  __shared__ uint8_t s_order[64];
-  __shared__ unsigned long long s_need;
-  __shared__ long long s_o;
-  __shared__ float4 s_off[27];
-  __shared__ unsigned long long s_bb[F32_WARPS][6];
-  __shared__ unsigned s_pre[F32_WARPS][28], s_st[F32_WARPS][28];
-  extern __shared__ __align__(16) unsigned char dyn_smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float4 *const sc = (float4 *)(dyn_smem + (size_t)warp * F32_WARP_SMEM);  // staged candidates
-  float4 *const ag = sc + F32_CHUNK;                                       // the group's agents
-  float4 *const acc = ag + 32;                                             // their sums (f, scale)
-  double *const pos_s = (double *)(acc + 32);                              // their P_t (x, y, z rows)
-  uint32_t *const skj = (uint32_t *)(pos_s + 96);                          // staged: sorted index
-  uint32_t *const ring = skj + F32_CHUNK;                                  // (agent << 16) | chunk index
-  float *const bnd = (float *)(ring + F32_RING);                           // summed error bounds
-  uint32_t *const nnb_s = (uint32_t *)(bnd + 32);                          // neighbour counts
-  uint32_t *const nct_s = nnb_s + 32;                                      // contact counts
-  const size_t dbase = ((size_t)blockIdx.x * F32_WARPS + warp) * F32_DCAP;
-  float4 *const dc = B.defer_c + dbase;  // deferred: FP32 contribution, bound
-  uint2 *const dw = B.defer_w + dbase;   // deferred: sorted index, agent | kind
-
+__global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevParams P) {
+  __shared__ unsigned s_pre[FIX_WARPS][28], s_st[FIX_WARPS][28];
+  __shared__ unsigned long long s_bb[FIX_WARPS][6];
+  __shared__ float s_tkf[16], s_tgf[16];
+  __shared__ double s_tkd[16], s_tgd[16];
+  __shared__ float4 s_fc[FIX_WARPS][FIX_BATCH][32];
+  __shared__ unsigned s_fk[FIX_WARPS][FIX_BATCH][32];
+  __shared__ uint8_t s_fb[FIX_WARPS][FIX_BATCH][32];
   DevCounters *C = B.ctr;
   if (C->error) return;
-  const AgentSet &A = *B.A;  // read at the use sites: no registers held
-  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
-  const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
-  const long long n_occ = C->n_occ;
-  const long long step = C->step;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  unsigned c_static = 0, c_moved = 0, c_cand = 0, c_nbr = 0, c_cont = 0, c_exact = 0;
-  int wsim = -1;
-  int fetch_phase = 0;
-  if (threadIdx.x < 27) {
-    const int t = threadIdx.x;
-    s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
+  const unsigned long long nfix = C->fix_n;
+  if (nfix == 0) return;
+  if (threadIdx.x < 16) {
+    s_tkd[threadIdx.x] = P.type_k[threadIdx.x];
+    s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
+    s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
+    s_tgf[threadIdx.x] = (float)P.type_gamma[threadIdx.x];
   }
+  __syncthreads();
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const long long step = C->step;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
-
-  while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
-      s_next = 0;
-    }
-    __syncthreads();
-    const long long o = s_o;
-    if (o < 0) break;
+  __syncwarp();
+  unsigned c_static = 0, c_moved = 0, n_exact = 0;
+  int wsim = -1;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * FIX_WARPS + warp; e < nfix;
+       e += (unsigned long long)gridDim.x * FIX_WARPS) {
+    if (!BDM_IN(B.ctr, (long long)e < B.cap)) break;
+    const uint4 ent = B.fix[e];
+    const unsigned kq = ent.x;
+    const long long o = (long long)(ent.y >> 6);
+    if (!BDM_IN(B.ctr, o < C->n_occ && (long long)kq < C->n)) continue;
+    const int lb = (int)(ent.y & 63u);
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
-    if (threadIdx.x < 27) {
-      const int t = threadIdx.x;
-      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
-      int occ = -1;
-      unsigned long long dm = 0ull;
-      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
-        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
-        occ = B.brick_occ[rank];
-        if (use_static) dm = B.dirty[rank];
-      }
-      s_nocc[t] = occ;
-      s_ndirty[t] = dm;
-    }
-    if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
-    if (threadIdx.x == 32) s_need = use_static ? B.need[o] : ~0ull;
-    __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
-
-    const double dt = G.dt;
-    const float dt_f = G.dt_f;
-    // the warps take the brick's boxes heaviest first (fewest idle warps at
-    // the brick's end): rank by agent count, ties by box index
-    if (threadIdx.x < 64) {
-      const unsigned c = s_bcnt[threadIdx.x];
-      unsigned r = 0;
-      for (int q = 0; q < 64; ++q) {
-        const unsigned cq = s_bcnt[q];
-        r += (cq > c) || (cq == c && q < (int)threadIdx.x);
-      }
-      s_order[r] = (uint8_t)threadIdx.x;
-    }
-    __syncthreads();
-
-    while (true) {
-      int kb = 0;
-      if (lane == 0) kb = atomicAdd(&s_next, 1);
-      kb = __shfl_sync(0xffffffffu, kb, 0);
-      if (kb >= 64) break;
-      const int lb = s_order[kb];
-      if (!((s_need >> lb) & 1ull)) continue;  // nothing left after the static pass
-      const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
-      if (nq == 0) continue;
-      int lx, ly, lz;
-      local_decode(lb, lx, ly, lz);
-      unsigned nb_st = 0, nb_cnt = 0;
-      bool nb_dirty = false;
-      if (lane < 27) {
-        const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
-        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
-                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
-        const int lc = local_code(ax & 3, ay & 3, az & 3);
-        const int occ = s_nocc[bo];
+    // the 27 stencil boxes (canonical order) and their agent ranges
+    int lx, ly, lz;
+    local_decode(lb, lx, ly, lz);
+    unsigned nb_st = 0, nb_cnt = 0;
+    if (lane < 27) {
+      const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
+      const int X = info.x + ((ax < 0) ? -1 : (ax > 3 ? 1 : 0));
+      const int Y = info.y + ((ay < 0) ? -1 : (ay > 3 ? 1 : 0));
+      const int Z = info.z + ((az < 0) ? -1 : (az > 3 ? 1 : 0));
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
+        const int occ = B.brick_occ[rank];
         if (occ >= 0) {
+          const int lc = local_code(ax & 3, ay & 3, az & 3);
           nb_st = B.box_start[(long long)occ * 64 + lc];
           nb_cnt = B.box_cnt[(long long)occ * 64 + lc];
         }
-        nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
-      }
-      const bool clean = !__any_sync(0xffffffffu, nb_dirty);
-      unsigned pre = nb_cnt;
-      for (int of = 1; of < 32; of <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
-        if (lane >= of) pre += y;
-      }
-      const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
-      if (lane < 27) {
-        s_pre[warp][lane] = pre - nb_cnt;
-        s_st[warp][lane] = nb_st;
-      }
-      __syncwarp();
-
-      for (unsigned q0 = 0; q0 < nq; q0 += 32) {
-        const unsigned ng = min(32u, nq - q0);
-        const bool valid = (unsigned)lane < ng;
-        const unsigned kq = qbase + q0 + (valid ? (unsigned)lane : 0u);
-        const uint32_t iq = B.perm[kq];
-        const float4 cq = B.c32[kq];
-        const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
-        const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
-        const bool compute = valid && !is_static;
-        ag[lane] = cq;
-        acc[lane] = make_float4(0.f, 0.f, 0.f, 0.f);
-        bnd[lane] = 0.f;
-        nnb_s[lane] = 0u;
-        nct_s[lane] = 0u;
-        if (MODE == FM_STEP && valid && !is_static) {
-          // the epilogue's P_t, fetched while the pairs are evaluated
-          const unsigned sa = (unsigned)__cvta_generic_to_shared(pos_s + lane);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(A.x[cur] + iq) : "memory");
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa + 256u), "l"(A.y[cur] + iq) : "memory");
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa + 512u), "l"(A.z[cur] + iq) : "memory");
-          asm volatile("cp.async.commit_group;\n" ::: "memory");
-        }
-        const unsigned cmask = __ballot_sync(0xffffffffu, compute);
-        __syncwarp();
-        if (cmask) {
-          unsigned dlen = 0;
-          // evaluate cnt (<= 32) ring pairs starting at ring position h
-          auto drain = [&](unsigned h, unsigned cnt) {
-            const bool v = (unsigned)lane < cnt;
-            const unsigned ent = v ? ring[(h & (F32_RING - 1)) + (unsigned)lane] : 0u;
-            const unsigned a = ent >> 16, i = ent & 0xffffu;
-            const float4 q = ag[a];
-            const float4 c = sc[i];
-            const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
-            const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-            const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
-            const float s = q.w + c.w, s2 = s * s;
-            const float W = fmaf(s, P.cband1, s2 * P.cband2);
-            const bool exact = v && (band || (d2 > s2 - W && d2 < s2 + W));
-            const bool cont = v && !exact && d2 <= s2 - W;
-            float vx = 0.f, vy = 0.f, vz = 0.f, vs = 0.f, vb = 0.f;
-            bool graze = false;
-            if (cont) {
-              const float inv_d = rsqrtf(d2);
-              const float d = d2 * inv_d;
-              const float delta = s - d;
-              const float rbar = __fdividef(q.w * c.w, s);
-              const float rd = rbar * delta;
-              const float sq = rd * rsqrtf(rd);
-              const float kd = P.kf * delta, gs = P.gammaf * sq;
-              const float scf = (kd - gs) * inv_d;
-              vx = scf * ex;
-              vy = scf * ey;
-              vz = scf * ez;
-              vs = kd + gs;
-              graze = delta < P.graze;
-              if (graze) {
-                // d/d(delta) of sqrt(rbar delta) is large: bound its FP32 error
-                vb = (sq > 1e-18f) ? fminf(P.gammaf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
-                                           P.gammaf * sqrtf(rbar * P.graze_e))
-                                   : P.gammaf * sqrtf(rbar * P.graze_e);
-              }
-            }
-            const bool defer = exact || graze;
-            const unsigned dbal = __ballot_sync(0xffffffffu, defer);
-            if (dbal) {
-              if (dlen + (unsigned)__popc(dbal) > F32_DCAP) {
-                // full list: settle it now, redoing every grazing pair in it
-                c_exact += settle_deferred(ExactSrc{B.perm, A.x[cur], A.y[cur], A.z[cur], B.c32, P.R2, P.k, P.gamma},
-                                           qbase + q0, dlen, 0xffffffffu, dc, dw, acc, bnd, nnb_s, nct_s);
-                dlen = 0;
-              }
-              if (defer) {
-                const unsigned p = dlen + (unsigned)__popc(dbal & lt_mask);
-                dc[p] = make_float4(vx, vy, vz, vb);
-                dw[p] = make_uint2(skj[i], a | (exact ? DA_EXACT : 0u));
-              }
-              dlen += (unsigned)__popc(dbal);
-            }
-            const unsigned nbal = __ballot_sync(0xffffffffu, v && !exact);
-            const unsigned cbal = __ballot_sync(0xffffffffu, cont);
-            // segmented reduction over runs of equal agent index
-            const unsigned key = v ? a : 32u + (unsigned)lane;
-            const unsigned prev = __shfl_up_sync(0xffffffffu, key, 1);
-            const bool is_head = lane == 0 || prev != key;
-            const unsigned heads = __ballot_sync(0xffffffffu, is_head);
-            const unsigned above = heads & ~(0xffffffffu >> (31 - lane));
-            const unsigned end = above ? (unsigned)(__ffs(above) - 1) : 32u;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-              const float tx = __shfl_down_sync(0xffffffffu, vx, off);
-              const float ty = __shfl_down_sync(0xffffffffu, vy, off);
-              const float tz = __shfl_down_sync(0xffffffffu, vz, off);
-              const float ts = __shfl_down_sync(0xffffffffu, vs, off);
-              const float tb = __shfl_down_sync(0xffffffffu, vb, off);
-              if ((unsigned)lane + off < end) { vx += tx; vy += ty; vz += tz; vs += ts; vb += tb; }
-            }
-            const unsigned segm = (end == 32u ? 0xffffffffu : ((1u << end) - 1u)) & ~lt_mask;
-            // a run whose agent is not above the previous run's starts a new
-            // epoch; within an epoch the runs' agents are distinct
-            const unsigned desc = __ballot_sync(0xffffffffu, is_head && lane > 0 && key < prev);
-            const unsigned ep = (unsigned)__popc(desc & (lt_mask | (1u << lane)));
-            const unsigned nep = (unsigned)__popc(desc);
-            for (unsigned e = 0; e <= nep; ++e) {
-              if (is_head && v && ep == e) {
-                float4 t = acc[a];
-                t.x += vx; t.y += vy; t.z += vz; t.w += vs;
-                acc[a] = t;
-                bnd[a] += vb;
-                nnb_s[a] += (unsigned)__popc(nbal & segm);
-                nct_s[a] += (unsigned)__popc(cbal & segm);
-              }
-              __syncwarp();
-            }
-          };
-
-          // Producer/consumer loop: scan (agent, 32-candidate block) steps
-          // until the ring holds 32 pairs, then evaluate one ring window.  A
-          // chunk is restaged only once the ring is empty (its entries index
-          // the staged chunk).
-          unsigned head = 0, tail = 0;
-          const unsigned own0 = s_pre[warp][13] + q0;  // stencil position of agent q0 itself
-          unsigned cnext = 0, cstart = 0, fill = 0, nblk = 0, am = 0, a = 0, b = 0, own = 0;
-          float4 q = make_float4(0.f, 0.f, 0.f, 0.f);
-          while (true) {
-            while (tail - head < 32u) {
-              if (am == 0) {
-                if (cnext >= ctot || tail != head) break;
-                // stage the next chunk (coalesced copies, box offset applied)
-                cstart = cnext;
-                fill = min((unsigned)F32_CHUNK, ctot - cstart);
-                cnext += fill;
-                __syncwarp();
-                for (unsigned g0 = 0; g0 < fill; g0 += 128u) {
-                  unsigned kjs[4];
-                  int boxs[4];
-#pragma unroll
-                  for (int m = 0; m < 4; ++m) {
-                    const unsigned p = cstart + g0 + lane + 32u * m;
-                    int lo = 0;
-#pragma unroll
-                    for (int st = 16; st > 0; st >>= 1)
-                      if (lo + st <= 26 && s_pre[warp][lo + st] <= p) lo += st;
-                    boxs[m] = lo;
-                    kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
-                  }
-                  float4 cs[4];
-#pragma unroll
-                  for (int m = 0; m < 4; ++m)
-                    if (g0 + lane + 32u * m < fill) cs[m] = __ldg(&B.c32[kjs[m]]);
-#pragma unroll
-                  for (int m = 0; m < 4; ++m) {
-                    const unsigned t = g0 + lane + 32u * m;
-                    if (t < fill) {
-                      const float4 of = s_off[boxs[m]];
-                      sc[t] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
-                      skj[t] = kjs[m];
-                    }
-                  }
-                }
-                __syncwarp();
-                if (lane == 0) c_cand += (unsigned)__popc(cmask) * fill;
-                nblk = (fill + 31u) >> 5;
-                am = cmask;
-                b = 0;
-                a = (unsigned)(__ffs(am) - 1);
-                q = ag[a];
-                own = own0 + a - cstart;
-              }
-              // eight (or, for the last few, four) candidate blocks of agent a
-              // per step: independent chains
-              auto scan_step = [&](auto width) {
-                constexpr int NW = decltype(width)::value;
-                unsigned bal[NW];
-#pragma unroll
-                for (int u = 0; u < NW; ++u) {
-                  const unsigned i = (b + u) * 32u + (unsigned)lane;
-                  const float4 c = sc[min(i, (unsigned)F32_CHUNK - 1u)];
-                  const float ex = q.x - c.x, ey = q.y - c.y, ez = q.z - c.z;
-                  const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-                  bal[u] = __ballot_sync(0xffffffffu, i < fill && d2 < P.R2_hi_f && i != own);
-                }
-#pragma unroll
-                for (int u = 0; u < NW; ++u) {
-                  if ((bal[u] >> lane) & 1u)
-                    ring[(tail + (unsigned)__popc(bal[u] & lt_mask)) & (F32_RING - 1)] = (a << 16) | ((b + u) * 32u + lane);
-                  tail += (unsigned)__popc(bal[u]);
-                }
-                b += NW;
-              };
-              if (nblk - b > 4u) scan_step(std::integral_constant<int, 8>());
-              else scan_step(std::integral_constant<int, 4>());
-              if (b >= nblk) {
-                b = 0;
-                am &= am - 1;
-                if (am) {
-                  a = (unsigned)(__ffs(am) - 1);
-                  q = ag[a];
-                  own = own0 + a - cstart;
-                }
-              }
-            }
-            // the producer stops short of 32 pairs only to restage or finish
-            const bool flush = tail - head < 32u;
-            const unsigned cnt = min(32u, tail - head);
-            if (cnt) {
-              __syncwarp();
-              drain(head, cnt);
-            }
-            if (flush) {
-              head = tail = 0;  // the ring is empty now
-              if (am == 0 && cnext >= ctot) break;
-            } else {
-              head += 32u;
-            }
-          }
-          if (dlen) {
-            // end of the group: refine the agents whose bound is too large
-            const float4 t = acc[lane];
-            const unsigned rmask = __ballot_sync(0xffffffffu, bnd[lane] > 0.25f * (P.rel_tol * t.w + P.abs_tol));
-            c_exact += settle_deferred(ExactSrc{B.perm, A.x[cur], A.y[cur], A.z[cur], B.c32, P.R2, P.k, P.gamma},
-                                       qbase + q0, dlen, rmask, dc, dw, acc, bnd, nnb_s, nct_s);
-          }
-        }
-        if (valid && !is_static) {  // static agents were finished by the static pass
-          const float4 t = acc[lane];
-          const unsigned nnb = nnb_s[lane], ncont = nct_s[lane];
-          c_nbr += nnb;
-          c_cont += ncont;
-          double px = 0.0, py = 0.0, pz = 0.0;
-          if (MODE == FM_STEP) {
-            // P_t, copied to shared memory asynchronously at the group's start
-            asm volatile("cp.async.wait_all;\n" ::: "memory");
-            px = pos_s[lane];
-            py = pos_s[32 + lane];
-            pz = pos_s[64 + lane];
-          }
-          finish_agent<1, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, is_static, t.x, t.y, t.z, 0.0, 0.0, 0.0,
-                                nnb, ncont, c_static, c_moved, s_bb[warp], px, py, pz);
-        }
       }
     }
+    unsigned pre = nb_cnt;
+    for (int of = 1; of < 32; of <<= 1) {
+      const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
+      if (lane >= of) pre += y;
+    }
+    const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
+    if (lane < 27) {
+      s_pre[warp][lane] = pre - nb_cnt;
+      s_st[warp][lane] = nb_st;
+    }
+    __syncwarp();
+    const float4 cq = B.c32[kq];
+    const dbl4 dq = exact_of<1>(B, A, cur, kq);
+    const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;
+    double fx = 0.0, fy = 0.0, fz = 0.0;
+    float gx = 0.f, gy = 0.f, gz = 0.f;
+    for (unsigned p0 = lane; p0 < ctot; p0 += 32u * FIX_BATCH) {
+      // FIX_BATCH candidates per lane: their loads in flight together, the
+      // records kept in shared memory for the evaluation loop
+      {
+        unsigned kjv[FIX_BATCH];
+        int bxv[FIX_BATCH];
+        float4 cv[FIX_BATCH];
+#pragma unroll
+        for (int u = 0; u < FIX_BATCH; ++u) {
+          const unsigned p = p0 + 32u * u;
+          int bx = 0;
+          for (int st = 16; st > 0; st >>= 1)
+            if (bx + st <= 26 && s_pre[warp][bx + st] <= p) bx += st;
+          bxv[u] = bx;
+          kjv[u] = s_st[warp][bx] + (p - s_pre[warp][bx]);
+        }
+#pragma unroll
+        for (int u = 0; u < FIX_BATCH; ++u)
+          if (p0 + 32u * u < ctot) cv[u] = __ldg(&B.c32[kjv[u]]);
+#pragma unroll
+        for (int u = 0; u < FIX_BATCH; ++u) {
+          s_fc[warp][u][lane] = cv[u];
+          s_fk[warp][u][lane] = kjv[u];
+          s_fb[warp][u][lane] = (uint8_t)bxv[u];
+        }
+      }
+      for (int u = 0; u < FIX_BATCH; ++u) {
+      if (p0 + 32u * u >= ctot) break;
+      const unsigned kj = s_fk[warp][u][lane];
+      const int bx = (int)s_fb[warp][u][lane];
+      if (kj == kq) continue;
+      if (!BDM_IN(B.ctr, (long long)kj < C->n)) continue;
+      const float4 c = s_fc[warp][u][lane];
+      const float ofx = (float)(bx % 3 - 1) * P.Lf, ofy = (float)((bx / 3) % 3 - 1) * P.Lf,
+                  ofz = (float)(bx / 9 - 1) * P.Lf;
+      const float ex = cq.x - (c.x + ofx), ey = cq.y - (c.y + ofy), ez = cq.z - (c.z + ofz);
+      const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
+      if (d2 >= P.R2_hi_f) continue;  // certainly no neighbour
+      const float s = cq.w + c.w, s2 = s * s;
+      const float W = fmaf(s, P.cband1, s2 * P.cband2);
+      const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+      if (!band && d2 >= s2 + W) continue;  // certainly no contact
+      const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
+      bool exact = band || d2 > s2 - W || d2 < P.close2;
+      if (!exact) {
+        // a certain contact: the force kernel's FP32 arithmetic
+        const float inv_d = rsqrtf(d2);
+        const float delta = s - d2 * inv_d;
+        const float rbar = __fdividef(cq.w * c.w, s);
+        const float rd = rbar * delta;
+        const float sq = rd * rsqrtf(rd);
+        const float fm = s_tkf[ab] * delta - s_tgf[ab] * sq;
+        exact = delta < P.graze || fabsf(fm) < P.low_scale;
+        if (!exact) {
+          const float scf = fm * inv_d;
+          gx = fmaf(scf, ex, gx);
+          gy = fmaf(scf, ey, gy);
+          gz = fmaf(scf, ez, gz);
+          continue;
+        }
+      }
+      n_exact++;
+      pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, exact_of<1>(B, A, cur, kj), fx, fy, fz);
+      }
+    }
+    fx += (double)gx;
+    fy += (double)gy;
+    fz += (double)gz;
+    for (int of = 16; of > 0; of >>= 1) {
+      fx += __shfl_xor_sync(0xffffffffu, fx, of);
+      fy += __shfl_xor_sync(0xffffffffu, fy, of);
+      fz += __shfl_xor_sync(0xffffffffu, fz, of);
+    }
+    const unsigned ncont = ent.z, nnb = ent.w;
+    if (lane == 0) {
+      const uint32_t iq = B.perm[kq];
+      double px = 0.0, py = 0.0, pz = 0.0;
+      if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
+      finish_agent<1, MODE>(B, P, A, cur, nxt, step, G.dt, G.dt_f, iq, A.flags[iq], false, (float)fx, (float)fy,
+                            (float)fz, 0.0, 0.0, 0.0, nnb, ncont, c_static, c_moved, s_bb[warp], px, py, pz);
+    }
+    __syncwarp();
   }
-  if (MODE == FM_STEP) asm volatile("cp.async.wait_all;\n" ::: "memory");  // none left in flight at exit
   if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
-  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = wsum64(c_cand),
-                           t_nbr = wsum64(c_nbr), t_cont = wsum64(c_cont), t_exact = wsum64(c_exact);
+  const unsigned long long t_moved = wsum64(c_moved), t_exact = wsum64(n_exact);
   if (lane == 0) {
-    if (t_static) atomicAdd(&C->a_static, t_static);
     if (t_moved) atomicAdd(&C->a_moved, t_moved);
-    if (t_cand) atomicAdd(&C->a_cand, t_cand);
-    if (t_nbr) atomicAdd(&C->a_nbr, t_nbr);
-    if (t_cont) atomicAdd(&C->a_contact, t_cont);
     if (t_exact) atomicAdd(&C->a_exact, t_exact);
   }
-}
-
-__global__ void k_reset_work(DevBufs B) {
-  B.ctr->work_next = 0;
-  B.ctr->heavy_take[0] = B.ctr->heavy_take[1] = 0;
 }
 
 // ---------------------------------------------------------------- division merge
@@ -1558,6 +1348,13 @@ __device__ unsigned blk_scan(unsigned v, unsigned *sm, unsigned *total) {
   return base + x - v;
 }
 
+// Per tile of SCAN_TILE agents: the number of dividing agents (low 16 bits)
+// and of removed agents (high 16 bits) in one packed word (a tile holds at
+// most 2048 of each, so the halves never carry into each other).
+__device__ __forceinline__ unsigned commit_flags(uint8_t f) {
+  return ((f & FL_DIVIDE) ? 1u : 0u) | ((f & FL_REMOVE) ? 0x10000u : 0u);
+}
+
 __global__ void k_div_reduce(DevBufs B) {
   __shared__ unsigned sm[32];
   const DevCounters *C = B.ctr;
@@ -1569,29 +1366,43 @@ __global__ void k_div_reduce(DevBufs B) {
   unsigned c = 0;
   for (int e = 0; e < SCAN_TILE / SCAN_THREADS; ++e) {
     const long long i = t0 + threadIdx.x * (SCAN_TILE / SCAN_THREADS) + e;
-    if (i < n) c += (A.flags[i] & FL_DIVIDE) ? 1u : 0u;
+    if (i < n) c += commit_flags(A.flags[i]);
   }
   unsigned tot;
   blk_scan(c, sm, &tot);
-  if (threadIdx.x == 0) B.scan_a[blockIdx.x] = tot;
+  if (threadIdx.x == 0) {
+    B.scan_a[blockIdx.x] = tot & 0xffffu;
+    B.scan_b[blockIdx.x] = tot >> 16;
+  }
 }
 
+// Exclusive scans over the tiles of the division counts (scan_a) and the
+// removal counts (scan_b); totals n_div and n_rm; the size after the commit
+// m = n + n_div - n_rm.
 __global__ void k_div_top(DevBufs B) {
   __shared__ unsigned sm[32];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const long long n = C->n;
   const long long nblk = (n + SCAN_TILE - 1) / SCAN_TILE;
-  unsigned carry = 0;
+  unsigned carry = 0, carry_rm = 0;
   for (long long b0 = 0; b0 < nblk; b0 += blockDim.x) {
     const long long b = b0 + threadIdx.x;
     const unsigned v = (b < nblk) ? B.scan_a[b] : 0u;
-    unsigned t;
+    const unsigned w = (b < nblk) ? B.scan_b[b] : 0u;
+    unsigned t, t_rm;
     const unsigned e = blk_scan(v, sm, &t);
-    if (b < nblk) B.scan_a[b] = carry + e;
+    const unsigned e_rm = blk_scan(w, sm, &t_rm);
+    if (b < nblk) { B.scan_a[b] = carry + e; B.scan_b[b] = carry_rm + e_rm; }
     carry += t;
+    carry_rm += t_rm;
   }
-  if (threadIdx.x == 0) C->n_div = carry;
+  if (threadIdx.x == 0) {
+    C->n_div = carry;
+    C->n_rm = carry_rm;
+    C->rm_m = n + (long long)carry - (long long)carry_rm;
+    C->rm_h = 0;
+  }
 }
 
 __global__ void k_div_write(DevBufs B, DevParams P) {
@@ -1640,12 +1451,120 @@ __global__ void k_div_write(DevBufs B, DevParams P) {
   flush_bbox(B, P, nxt, 0, bmin, bmax);
 }
 
+// ---------------------------------------------------------------- removal
+// Removal (Sec. 3.2), after the daughters are appended: the vector of
+// n' = n + n_div agents keeps no empty element.  With m = n' - n_rm the new
+// size, a removed agent at i < m is a hole; the survivors at i >= m fill the
+// holes, the k-th survivor (ascending index) the k-th hole (ascending index),
+// which is the paper's swap step with the removed list in storage order.
+// The work is O(n) flag reads (one byte per agent) for the holes, and
+// O(n_rm) for the moves.  The removed agents' positions P_t are kept as
+// ghosts: their boxes are dirty in the next iteration's static test.
+__global__ void k_rm_holes(DevBufs B, DevParams P) {
+  __shared__ unsigned sm[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  const long long t0 = (long long)blockIdx.x * SCAN_TILE;
+  if (t0 >= n) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1);
+  const long long m = C->rm_m;
+  constexpr int E = SCAN_TILE / SCAN_THREADS;
+  unsigned c = 0;
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i < n) c += (A.flags[i] & FL_REMOVE) ? 1u : 0u;
+  }
+  unsigned tot;
+  unsigned r = blk_scan(c, sm, &tot) + B.scan_b[blockIdx.x];
+  unsigned holes = 0;
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i >= n || !(A.flags[i] & FL_REMOVE)) continue;
+    B.ghost[r] = mk_dbl4(A.x[cur][i], A.y[cur][i], A.z[cur][i], 0.0);
+    if (i < m) {
+      B.bucket[r] = (uint32_t)i;
+      holes = r + 1;
+    }
+    ++r;
+  }
+  if (holes) atomicMax(&C->rm_h, (unsigned long long)holes);
+}
+
+__device__ __forceinline__ void move_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, long long src,
+                                           long long dst) {
+  for (int b = 0; b < 2; ++b) {
+    A.x[b][dst] = A.x[b][src];
+    A.y[b][dst] = A.y[b][src];
+    A.z[b][dst] = A.z[b][src];
+  }
+  if (P.precision == 0) ((double *)A.diam)[dst] = ((const double *)A.diam)[src];
+  else ((float *)A.diam)[dst] = ((const float *)A.diam)[src];
+  if (A.vol) A.vol[dst] = A.vol[src];
+  A.uid[dst] = A.uid[src];
+  A.beh[dst] = A.beh[src];
+  A.flags[dst] = A.flags[src];
+  A.nz[dst] = A.nz[src];
+  if (P.keep_forces)
+    for (int d = 0; d < 3; ++d) B.fdbg[(size_t)d * B.cap + dst] = B.fdbg[(size_t)d * B.cap + src];
+}
+
+// The survivors at i in [m, n'): block b takes the b-th tile that meets the
+// tail.  Survivor i is the k-th of the tail, k = (i - m) - (removed agents in
+// [m, i)).  Only flags at indices >= m are read: the moves write holes, all
+// below m, concurrently.  For a tile starting at t0 > m, the removed agents in
+// [m, t0) are rr(t0) - h, with rr(t0) = the tile's exclusive removal prefix
+// and h the number of holes (removed agents below m).
+__global__ void k_rm_move(DevBufs B, DevParams P) {
+  __shared__ unsigned sm[32];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const long long n = C->n;
+  const long long n2 = n + C->n_div;
+  const long long m = C->rm_m;
+  if (m >= n2) return;
+  const long long tile = m / SCAN_TILE + blockIdx.x;
+  const long long t0 = tile * SCAN_TILE;
+  if (t0 >= n2) return;
+  const AgentSet A = *B.A;
+  const long long ntiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  const long long h = (long long)C->rm_h;
+  constexpr int E = SCAN_TILE / SCAN_THREADS;
+  unsigned c = 0;
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i >= m && i < n) c += (A.flags[i] & FL_REMOVE) ? 1u : 0u;
+  }
+  unsigned tot;
+  long long before = 0;  // removed agents in [m, t0)
+  if (t0 > m) before = ((tile < ntiles) ? (long long)B.scan_b[tile] : (long long)C->n_rm) - h;
+  long long rt = (long long)blk_scan(c, sm, &tot) + before;
+  for (int e = 0; e < E; ++e) {
+    const long long i = t0 + threadIdx.x * E + e;
+    if (i >= n2) break;
+    if (i < m) continue;
+    const bool removed = i < n && (A.flags[i] & FL_REMOVE);
+    if (!removed) {
+      const long long k = (i - m) - rt;
+      if (!BDM_IN(B.ctr, k >= 0 && k < h)) break;
+      const long long dst = (long long)B.bucket[k];
+      if (!BDM_IN(B.ctr, dst < m)) break;
+      move_agent(B, P, A, i, dst);
+    }
+    rt += removed ? 1 : 0;
+  }
+}
+
 __global__ void k_finish(DevBufs B) {
   DevCounters *C = B.ctr;
   if (C->error) return;
-  const long long nd = C->n_div;
-  C->n += nd;
+  const long long nd = C->n_div, nr = C->n_rm;
+  C->n += nd - nr;
   C->next_uid += (unsigned long long)nd;
+  C->l_rm = (unsigned long long)nr;
+  C->l_fix = C->fix_n;
+  C->n_ghost = nr;
   C->l_static = C->a_static;
   C->l_moved = C->a_moved;
   C->l_cand = C->a_cand;
@@ -1683,18 +1602,6 @@ __global__ void k_nbr_offsets(DevBufs B) {
 void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
   k_reset_work<<<1, 1, 0, s>>>(B);
   if (mode == FM_STEP && P.detect_static) k_static<<<2 * c.occ_blocks, KS_WARPS * 32, 0, s>>>(B, P);
-  if (P.precision == 1 && P.lanes_fixed == 0 && (mode == FM_STEP || mode == FM_FORCES)) {
-    // the FP32 form's pair-ring kernel (dynamic shared memory above 48 KB)
-    constexpr int smem = F32_WARPS * F32_WARP_SMEM;
-    if (mode == FM_STEP) {
-      cudaFuncSetAttribute(k_force32<FM_STEP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      k_force32<FM_STEP><<<c.force32_blocks, F32_WARPS * 32, smem, s>>>(B, P);
-    } else {
-      cudaFuncSetAttribute(k_force32<FM_FORCES>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-      k_force32<FM_FORCES><<<c.force32_blocks, F32_WARPS * 32, smem, s>>>(B, P);
-    }
-    return;
-  }
   const int g = c.force_blocks;
 #define LF(PR, MO) k_force<PR, MO><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
   if (P.precision == 0) {
@@ -1707,7 +1614,7 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
   } else {
     switch (mode) {
       case FM_STEP:
-        if (!P.walk && !P.grow) k_force<1, FM_STEP, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, P);
+        if (!P.walk && !P.grow && !P.die) k_force<1, FM_STEP, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, P);
         else LF(1, FM_STEP);
         break;
       case FM_FORCES: LF(1, FM_FORCES); break;
@@ -1716,13 +1623,32 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
     }
   }
 #undef LF
+  if (mode == FM_FORCES) launch_force_fix(B, P, c, mode, s);
 }
 
+// the FP64 fix-up pass of the FP32 form, after launch_force (FM_STEP: its own
+// phase of an iteration; FM_FORCES: part of launch_force)
+void launch_force_fix(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
+  if (P.precision != 1) return;
+  if (mode == FM_STEP) k_force_fix<FM_STEP><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
+  if (mode == FM_FORCES) k_force_fix<FM_FORCES><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
+}
+
+int force_launches(const DevParams &P) { (void)P; return 2; }
+int force_fix_launches(const DevParams &P) { return P.precision == 1 ? 1 : 0; }
+
 void launch_divide(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
+  if (!P.grow && !P.die) return;
   k_div_reduce<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B);
   k_div_top<<<1, 1024, 0, s>>>(B);
-  k_div_write<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B, P);
+  if (P.grow) k_div_write<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B, P);
+  if (P.die) {
+    k_rm_holes<<<c.agent_scan_blocks, SCAN_THREADS, 0, s>>>(B, P);
+    k_rm_move<<<c.agent_scan_blocks + 1, SCAN_THREADS, 0, s>>>(B, P);
+  }
 }
+
+int divide_launches(const DevParams &P) { return (P.grow || P.die) ? 2 + (P.grow ? 1 : 0) + (P.die ? 2 : 0) : 0; }
 
 void launch_finish(const DevBufs &B, const DevParams &P, cudaStream_t s) {
   (void)P;

@@ -231,8 +231,12 @@ __global__ void k_brick_rank(DevBufs B, DevParams P) {
 __device__ __forceinline__ void box_key(const DevBufs &B, const SimGeom &G, int bx, int by, int bz, int &rank,
                                         int &lc) {
   const int Bx = bx >> 2, By = by >> 2, Bz = bz >> 2;
-  const long long lin = ((long long)Bz * G.nr[1] + By) * G.nr[0] + Bx;
+  long long lin = ((long long)Bz * G.nr[1] + By) * G.nr[0] + Bx;
+  if (!BDM_IN(B.ctr, bx >= 0 && by >= 0 && bz >= 0 && Bx < G.nr[0] && By < G.nr[1] && Bz < G.nr[2] &&
+                         G.brick_base + lin < B.brick_cap))
+    lin = -G.brick_base;
   rank = B.brick_table[G.brick_base + lin];
+  if (!BDM_IN(B.ctr, rank >= 0 && rank < B.brick_cap)) rank = 0;
   lc = local_code(bx & 3, by & 3, bz & 3);
 }
 
@@ -283,7 +287,29 @@ __global__ void k_keys(DevBufs B, DevParams P) {
       }
     }
     if (P.grow && (A.beh[i] & BEH_GROW)) {
-      if (__dadd_rn(A.vol[i], P.growth) >= P.divide_volume) ndiv++;
+      // an agent removed in this iteration does not divide
+      if (__dadd_rn(A.vol[i], P.growth) >= P.divide_volume &&
+          !(P.die && (A.beh[i] & BEH_DIE) && agent_dies(P, A.uid[i], C->step)))
+        ndiv++;
+    }
+  }
+  if (use_static) {
+    // the boxes the agents removed in the previous iteration left (their
+    // position at its start) are dirty: their neighbours lost a neighbour
+    const long long ng = C->n_ghost;
+    const SimGeom &G = B.geom[0];
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < ng;
+         g += (long long)gridDim.x * blockDim.x) {
+      const dbl4 q = B.ghost[g];
+      bool fb;
+      const int ox = box_axis(q.x, G.lo[0], G.lo_f[0], P, fb);
+      const int oy = box_axis(q.y, G.lo[1], G.lo_f[1], P, fb);
+      const int oz = box_axis(q.z, G.lo[2], G.lo_f[2], P, fb);
+      if (ox >= 0 && ox < G.nb[0] && oy >= 0 && oy < G.nb[1] && oz >= 0 && oz < G.nb[2]) {
+        int r2, l2;
+        box_key(B, G, ox, oy, oz, r2, l2);
+        atomicOr(&B.dirty[r2], 1ull << l2);
+      }
     }
   }
   if (P.grow) {
@@ -394,7 +420,10 @@ __global__ void k_scatter(DevBufs B) {
   const long long n = C->n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t r = B.key[i] >> 6;
-    B.bucket[B.brick_start[r] + B.arrival[i]] = (uint32_t)i;
+    if (!BDM_IN(B.ctr, r < (uint32_t)B.brick_cap)) continue;
+    const unsigned long long dst = (unsigned long long)B.brick_start[r] + B.arrival[i];
+    if (!BDM_IN(B.ctr, dst < (unsigned long long)n)) continue;
+    B.bucket[dst] = (uint32_t)i;
   }
 }
 
@@ -429,6 +458,7 @@ __device__ __forceinline__ void write_compact(const DevBufs &B, const DevParams 
     r = ((const float *)A.diam)[i] * 0.5f;
   }
   B.c32[k] = make_float4(xl, yl, zl, r);
+  if (P.n_types > 1) B.tp[k] = (uint8_t)((A.beh[i] >> BEH_TYPE_SHIFT) & 3u);
 }
 
 // Agent idx at sorted position kk of occupied brick o: its storage index, its
@@ -436,6 +466,7 @@ __device__ __forceinline__ void write_compact(const DevBufs &B, const DevParams 
 // coordinates and simulation.
 __device__ __forceinline__ void place_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
                                             long long o, uint32_t idx, long long kk, bool first) {
+  if (!BDM_IN(B.ctr, kk >= 0 && kk < B.ctr->n && idx < (uint32_t)B.cap && o < B.occ_cap)) return;
   B.perm[kk] = idx;
   const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, idx);
   const SimGeom &G = B.geom[s];
@@ -476,7 +507,9 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
     if (threadIdx.x == 0) s_abort = 0;
     __syncthreads();
     for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+      if (!BDM_IN(B.ctr, (long long)S0 + k < B.ctr->n)) break;
       const uint32_t idx = B.bucket[S0 + k];
+      if (!BDM_IN(B.ctr, idx < (uint32_t)B.cap)) continue;
       const unsigned l = B.key[idx] & 63u;
       if (onchip) { s_idx[k] = idx; s_l[k] = (uint8_t)l; }
       atomicAdd(&s_cnt[l], 1u);
@@ -511,6 +544,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
       if (onchip) { idx = s_idx[k]; l = s_l[k]; }
       else { idx = B.bucket[S0 + k]; l = B.key[idx] & 63u; }
       const unsigned pos = atomicAdd(&s_cur[l], 1u);
+      if (!BDM_IN(B.ctr, pos < m && (!onchip || pos < BS_SMEM_M))) continue;
       if (onchip) { s_grp[pos] = idx; s_gl[pos] = (uint8_t)l; }
       else B.arrival[S0 + pos] = idx;
     }
@@ -560,6 +594,7 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     __syncwarp();
     for (unsigned k = lane; k < m; k += 32) {
       const uint32_t idx = B.bucket[S0 + k];
+      if (!BDM_IN(B.ctr, k < BSW_MAX && idx < (uint32_t)B.cap)) continue;
       const unsigned l = B.key[idx] & 63u;
       s_idx[w][k] = idx;
       s_l[w][k] = (uint8_t)l;
@@ -582,6 +617,7 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     for (unsigned k = lane; k < m; k += 32) {
       const unsigned l = s_l[w][k];
       const unsigned pos = atomicAdd(&s_cur[w][l], 1u);
+      if (!BDM_IN(B.ctr, pos < m && pos < BSW_MAX)) continue;
       s_grp[w][pos] = s_idx[w][k];
       s_gl[w][pos] = (uint8_t)l;
     }
@@ -611,6 +647,7 @@ __global__ void k_gather(DevBufs B, DevParams P) {
   const long long n = C->n;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const uint32_t i = B.perm[k];
+    if (!BDM_IN(B.ctr, (long long)i < n)) continue;
     for (int b = 0; b < 2; ++b) {
       D.x[b][k] = A.x[b][i];
       D.y[b][k] = A.y[b][i];

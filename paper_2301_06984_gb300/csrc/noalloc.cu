@@ -163,7 +163,6 @@ extern "C" int bdm_forces_noalloc(int64_t n, const double *xyz, const double *di
   lc.agent_scan_blocks = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
   lc.occ_blocks = 608;
   lc.force_blocks = 608;
-  lc.force32_blocks = 456;
 
   // state every call starts from: agent sets, counters (zero but n),
   // flags zero; the tables the kernels fill are rebuilt on every call

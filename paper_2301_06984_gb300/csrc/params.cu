@@ -35,6 +35,15 @@ DevParams make_dev_params(const bdm_params &P) {
   d.keep_forces = P.keep_forces ? 1 : 0;
   d.grow = P.growth_per_step > 0.0 ? 1 : 0;
   d.walk = P.walk_step > 0.0 ? 1 : 0;
+  d.death_prob = P.death_prob;
+  d.n_types = P.n_types > 1 ? P.n_types : 0;
+  for (int e = 0; e < 16; ++e) {
+    d.type_k[e] = d.n_types ? P.type_k[e] : P.k;
+    d.type_gamma[e] = d.n_types ? P.type_gamma[e] : P.gamma;
+  }
+  d.die = P.death_prob > 0.0 ? 1 : 0;
+  // u = k 2^-53 (k an integer below 2^53) is below p iff k < ceil(p 2^53)
+  d.death_thr = P.death_prob >= 1.0 ? (1ull << 53) : (uint64_t)std::ceil(P.death_prob * 9007199254740992.0);
   // fixed-point local coordinates: L 2^s < 2^29, box step a multiple of 128
   int lg = (int)std::ceil(std::log2(d.L * 1.0000001));
   int sft = 29 - lg;
@@ -74,9 +83,23 @@ DevParams make_dev_params(const bdm_params &P) {
     const double Rm = 1.01 * R;
     d.graze_e = (float)(std::sqrt(3.0) * Ec + (1.5 * pow2i(-24) + pow2i(-22) + pow2i(-24)) * Rm +
                         pow2i(-24) * (Rm + 2.0 * (double)d.graze));
+    // the difference vector's error is at most sqrt(3) Ec, so the unit
+    // direction of a pair at distance d is off by at most sqrt(3) Ec / d
+    d.dir_e = (float)(std::sqrt(3.0) * Ec);
+    // the fix-up pass evaluates pairs closer than 1 um in FP64: there the
+    // direction error dir_e / d of a pair exceeds 5e-6 of its force
+    d.close2 = 1.0f;
+    // grazing contacts shallower than 2e-3 um go to FP64 in place: above it
+    // the bound gamma sqrt(rbar) graze_e / (2 sqrt(delta)) of one contact
+    // stays near 2e-4, a small part of a dense agent's tolerance
+    d.graze_exact = 2e-3f;
   }
   d.rel_tol = 2e-5f;
   d.abs_tol = 1e-6f;
+  // below S = 4 abs_tol / rel_tol (0.2) the tolerance rel_tol S + abs_tol is
+  // under 5e-6, a few times the FP32 error of one contact (the coordinates'
+  // rounding, about 1e-6 um), so such agents are evaluated in FP64
+  d.low_scale = 4.0f * d.abs_tol / d.rel_tol;
   d.cband1 = (float)(4.0 * std::sqrt(3.0) * E);
   d.cband2 = (float)(10.0 * pow2i(-23));
   d.lanes_fixed = FORCE_LANES_DEFAULT;

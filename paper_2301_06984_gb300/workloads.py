@@ -13,6 +13,11 @@ displacement or division).  Both the CUDA path (tests, bench) and the oracle
               fraction cubes, d = 10 um, per-simulation dt U[0.005, 0.02]
   core_shell -- 150M agents: 90% on a static FCC core (0.6 volume fraction),
               10% random walkers in a surrounding shell, d = 10 um
+  cell_sorting -- two cell types mixed at random in a ball at 0.5 volume
+              fraction, diameters U[9,11] um; same-type pairs adhere more
+              strongly than mixed pairs (the differential-adhesion model class
+              of the paper's cell-sorting comparison, whose own parameters are
+              not published with it)
 """
 import math
 from dataclasses import dataclass, field
@@ -21,6 +26,8 @@ import numpy as np
 
 GROW = 1
 WALK = 2
+DIE = 4
+TYPE_SHIFT = 4
 
 
 @dataclass
@@ -180,3 +187,25 @@ def core_shell(n=150_000_000, seed=5, core_frac=0.9, lattice_const=15.17, diam=1
                  steps=steps, beh=beh)
     w.notes.update(n_core=n_core, n_shell=n_shell, r_core=r_core, r_out=r_out)
     return w
+
+
+# force constants of the two-type cell-sorting workload: k equal for all
+# pairs, the adhesion term gamma three times stronger between equal types
+SORTING_K = [[2.0, 2.0], [2.0, 2.0]]
+SORTING_GAMMA = [[1.5, 0.5], [0.5, 1.5]]
+
+
+def cell_sorting(n=10_000_000, seed=6, volume_fraction=0.5, dmin=9.0, dmax_=11.0, steps=20, precision="fp32"):
+    rng = np.random.default_rng(seed)
+    mean_vol = (math.pi / 6.0) * ((dmin + dmax_) / 2.0) ** 3
+    radius = (3.0 * n * mean_vol / volume_fraction / (4.0 * math.pi)) ** (1.0 / 3.0)
+    v = rng.normal(size=(3, n))
+    v /= np.linalg.norm(v, axis=0)
+    p = v * (radius * rng.uniform(0.0, 1.0, n) ** (1.0 / 3.0)) + (radius + 20.0)
+    d = _f32_exact(rng.uniform(dmin, dmax_, n))
+    types = rng.integers(0, 2, n).astype(np.uint8)
+    beh = (types << TYPE_SHIFT).astype(np.uint8)
+    R = float(dmax_)
+    params = dict(R=R, L=R, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.0, precision=precision,
+                  type_k=SORTING_K, type_gamma=SORTING_GAMMA, seed=seed)
+    return Workload("cell_sorting-%d" % n, p[0].copy(), p[1].copy(), p[2].copy(), d, params, steps=steps, beh=beh)

@@ -29,18 +29,20 @@ def test_library_exports_every_declared_symbol():
     for name in declared_functions():
         assert hasattr(L, name), name
     assert set(declared_functions()) <= set(bdm.SIGNATURES)
-    assert L.bdm_version() == 100
+    assert L.bdm_version() == 200
 
 
 def test_struct_layouts_match_header_sizes():
-    # bdm_params: 7 doubles, 4 int32, pointer, u64, 5 doubles, i64, 2 int32
-    assert C.sizeof(bdm.Params) == 7 * 8 + 4 * 4 + 8 + 8 + 5 * 8 + 8 + 2 * 4
-    assert C.sizeof(bdm.Counters) == 15 * 8 + 2 * 4
+    # bdm_params: 7 doubles, 4 int32, pointer, u64, 5 doubles, i64, 2 int32,
+    # death_prob, 2 int32, two tables of 16 doubles
+    assert C.sizeof(bdm.Params) == 7 * 8 + 4 * 4 + 8 + 8 + 5 * 8 + 8 + 2 * 4 + 8 + 2 * 4 + 32 * 8
+    assert C.sizeof(bdm.Counters) == 15 * 8 + 2 * 4 + 2 * 8
 
 
 @pytest.mark.parametrize("field,value", [("interaction_radius", 0.0), ("interaction_radius", -1.0),
                                          ("box_edge", 5.0), ("n_sims", 0), ("capacity", 0), ("precision", 7),
-                                         ("dt", -1.0), ("sort_every", -2)])
+                                         ("dt", -1.0), ("sort_every", -2), ("death_prob", -0.1),
+                                         ("death_prob", 1.5)])
 def test_create_rejects_bad_parameters_without_touching_the_gpu(field, value):
     L = bdm.lib()
     p = bdm.Params()
@@ -69,3 +71,12 @@ def test_null_handles_are_rejected():
     assert L.bdm_step(None, 1) == bdm.BDM_EINVAL
     assert L.bdm_sort(None) == bdm.BDM_EINVAL
     L.bdm_destroy(None)
+
+
+def test_removal_requires_single_simulation():
+    L = bdm.lib()
+    p = bdm.Params()
+    p.interaction_radius, p.dt, p.max_displacement, p.k, p.gamma = 10.0, 0.01, 3.0, 2.0, 1.0
+    p.n_sims, p.capacity, p.precision, p.death_prob = 4, 100, bdm.BDM_FP32_FORCE, 0.1
+    h = C.c_void_p()
+    assert L.bdm_create(C.byref(p), None, C.byref(h)) == bdm.BDM_EINVAL

@@ -647,3 +647,26 @@ def test_heterotypic_antisymmetry_and_type_dependence():
     assert np.abs(f.sum(axis=1)).max() <= 1e-12 * scale
     f_sw, _, _ = _state(p, d, beh=(beh ^ 0x10).astype(np.uint8)).forces_of(P)
     assert not np.array_equal(f, f_sw) and nz.sum() > 0
+
+
+# --------------------------------------------------------------------------- timing build
+def test_openmp_timing_build_gives_the_same_bits():
+    # the CPU baseline's parallel build of the oracle: each agent's sum stays
+    # serial, so a trajectory with static skip, removal and a sort step is
+    # bit-identical to the serial build's
+    from oracle import build_oracle
+    lib = build_oracle.build_omp()
+    if lib is None:
+        pytest.skip("no OpenMP in this compiler")
+    w = W.core_shell(n=6000, seed=5, precision="fp64")
+    w.beh = (w.beh | np.where(np.arange(w.n) % 5 == 0, 4, 0)).astype(np.uint8)
+    P = O.make_params(R=10.0, detect_static=1, walk_step=0.5, sort_every=3, death_prob=0.05, seed=5)
+    a = _state(np.stack([w.x, w.y, w.z]), w.diam, beh=w.beh)
+    a.step(P, 5)
+    with O.use_library(lib) as L:
+        assert L.orc_threads() >= 1
+        b = _state(np.stack([w.x, w.y, w.z]), w.diam, beh=w.beh)
+        b.step(P, 5)
+    assert np.array_equal(a.uid[: a.n], b.uid[: b.n])
+    assert np.array_equal(a.positions(), b.positions())
+    assert np.array_equal(a.nz[: a.n], b.nz[: b.n])

@@ -45,20 +45,27 @@ def test_lattice_47_cubed_20_iterations_bit_exact():
 
 
 def test_blobs_10M_sampled_forces_fp32():
-    # the GPU state after iterations 1, 10 and 100; the oracle computes the
-    # forces of sampled agents from that state
+    # iterations 1, 10 and 100 of the 10M-agent run: the forces the timed
+    # production kernel itself formed in that iteration (kept with
+    # keep_forces), for 3000 sampled agents, against the oracle's forces on the
+    # state the iteration started from; plus the force-only kernel on the
+    # state after iteration 100
     w = W.blobs()
-    s = H.gpu_sim(w, precision="fp32")
+    s = H.gpu_sim(w, precision="fp32", keep_forces=True)
+    P = H.oracle_params(w)
     rng = np.random.default_rng(0)
-    for steps in (1, 9, 90):
-        s.step(steps)
-        f_g, nz_g, nnb_g = s.forces_now()
-        a, o = _state_of(s)
-        q = _sample(rng, a["n"], 3000)
-        P = H.oracle_params(w)
-        f_o, nz_o, nnb_o, scale = o.forces_of(P, q=q, with_scale=True)
-        assert np.array_equal(nnb_g[q], nnb_o) and np.array_equal(nz_g[q], nz_o)
-        H.assert_fp32_forces(f_g[:, q], f_o, scale)
+    done = 0
+    for it in (1, 10, 100):
+        s.step(it - 1 - done)
+        q = _sample(rng, s.counters()["n_agents"], 3000)
+        H.production_step_vs_oracle(s, P, q=q, what="blobs 10M iteration %d, production kernel (3000 sampled)" % it)
+        done = it
+    f_g, nz_g, nnb_g = s.forces_now()
+    a, o = _state_of(s)
+    q = _sample(rng, a["n"], 3000)
+    f_o, nz_o, nnb_o, sc, sa = o.forces_of(P, q=q, with_scale=True, with_scale_abs=True)
+    assert np.array_equal(nnb_g[q], nnb_o) and np.array_equal(nz_g[q], nz_o)
+    H.assert_fp32_forces(f_g[:, q], f_o, sa, sc, what="blobs 10M after iteration 100, force-only kernel (3000)")
 
 
 def test_blobs_100k_positions_after_10_iterations_fp32():
@@ -71,8 +78,7 @@ def test_blobs_100k_positions_after_10_iterations_fp32():
     o.step(H.oracle_params(w), 10)
     pos, a = H.gpu_positions(s)
     assert np.array_equal(a["uid"], o.uid[: o.n])
-    err = np.abs(pos - o.positions()).max()
-    assert err <= 1e-4, err
+    H.assert_positions(pos, o.positions(), what="positions fp32 blobs 100k, 10 iterations")
 
 
 def test_ensemble_512_members_match_independent_runs_fp32():
@@ -86,7 +92,7 @@ def test_ensemble_512_members_match_independent_runs_fp32():
         lo, hi = w.sim_off[m], w.sim_off[m + 1]
         o = O.State(w.x[lo:hi], w.y[lo:hi], w.z[lo:hi], w.diam[lo:hi])
         o.step(O.make_params(R=10.0, dt=float(w.dt_sim[m])), 3)
-        assert np.abs(pos[:, lo:hi] - o.positions()).max() <= 1e-4, "simulation %d" % m
+        H.assert_positions(pos[:, lo:hi], o.positions(), what="positions fp32 ensemble-512 member %d, 3 it." % m)
 
 
 def test_core_shell_150M_static_fraction_and_subbox_forces():
@@ -109,7 +115,7 @@ def test_core_shell_150M_static_fraction_and_subbox_forces():
     assert inner.sum() > 1000
     o = O.State(pos[0, sel], pos[1, sel], pos[2, sel], a["diam"][sel])
     qi = np.nonzero(inner[sel])[0]
-    f_o, nz_o, nnb_o, scale = o.forces_of(H.oracle_params(w), q=qi, with_scale=True)
+    f_o, nz_o, nnb_o, sc, sa = o.forces_of(H.oracle_params(w), q=qi, with_scale=True, with_scale_abs=True)
     g = sel[qi]
     assert np.array_equal(nnb_g[g], nnb_o) and np.array_equal(nz_g[g], nz_o)
-    H.assert_fp32_forces(f_g[:, g], f_o, scale)
+    H.assert_fp32_forces(f_g[:, g], f_o, sa, sc, what="core+shell 150M sub-box, force-only kernel")
