@@ -18,6 +18,7 @@
  *   Sec. 3.2 (additions at end of iteration)-> division merge (parent order)
  *   Sec. 3.2 (removal in five steps)         -> orc_remove (swap from the tail)
  *   Sec. 4.2 (Morton order, gap/offset DFS)  -> orc_morton_offsets, sort step
+ *   Sec. 4.2 (Hilbert order, compared there) -> orc_hilbert3, orc_curve_order
  *   Sec. 5  (static-agent conditions i-iv)   -> static contract
  *   Sec. 5  defers the pair force to Cortex3D without a formula; the force
  *   used here is F = k*delta - gamma*sqrt(rbar*delta) along the centre line,
@@ -70,7 +71,7 @@ typedef struct {
   uint64_t seed;
   double death_prob;     /* per-iteration probability that a DIE agent is removed */
   int32_t n_types;       /* > 1: per-type-pair force constants below              */
-  int32_t pad;
+  int32_t curve;         /* storage order of the sort step: 0 Morton, 1 Hilbert   */
   double type_k[16];     /* k of the types (a, b) at [4 a + b]                    */
   double type_gamma[16]; /* gamma of the types (a, b) at [4 a + b]                */
 } orc_params;
@@ -187,6 +188,42 @@ double orc_cbrt(double x) {
     y = y - (y3 - m) / (3.0 * y2);
   }
   return sgn * ldexp(y, q);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hilbert index of the cell (x, y, z) of a 2^bits cube, by Skilling's        */
+/* transpose method (J. Skilling, "Programming the Hilbert curve", AIP Conf. */
+/* Proc. 707, 2004): going down from the top bit, undo on the lower bits the */
+/* reflection or the exchange of axes the curve applies in the sub-cube the */
+/* point lies in; Gray-encode the axes; then read the index with x's bit    */
+/* most significant in each 3-bit digit.                                    */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_hilbert3(uint64_t x, uint64_t y, uint64_t z, int bits) {
+  if (bits <= 0) return 0;
+  uint64_t X[3] = {x, y, z};
+  const uint64_t M = 1ULL << (bits - 1);
+  for (uint64_t Q = M; Q > 1; Q >>= 1) {
+    const uint64_t P = Q - 1;
+    for (int i = 0; i < 3; ++i) {
+      if (X[i] & Q) {
+        X[0] ^= P; /* reflect the lower bits of axis 0 */
+      } else {     /* exchange the lower bits of axes 0 and i */
+        const uint64_t t = (X[0] ^ X[i]) & P;
+        X[0] ^= t;
+        X[i] ^= t;
+      }
+    }
+  }
+  X[1] ^= X[0]; /* Gray encode */
+  X[2] ^= X[1];
+  uint64_t t = 0;
+  for (uint64_t Q = M; Q > 1; Q >>= 1)
+    if (X[2] & Q) t ^= Q - 1;
+  for (int i = 0; i < 3; ++i) X[i] ^= t;
+  uint64_t h = 0;
+  for (int b = bits - 1; b >= 0; --b)
+    for (int i = 0; i < 3; ++i) h = (h << 1) | ((X[i] >> b) & 1ULL);
+  return h;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -651,13 +688,48 @@ static void permute_f64(double *a, const int64_t *perm, int64_t n, double *tmp) 
   memcpy(a, tmp, sizeof(double) * (size_t)n);
 }
 
+/* Storage order of a sort step for the curve P->curve: perm[k] = storage
+ * index of the agent at sorted position k.  Morton: by the Morton code of the
+ * box.  Hilbert: by the Hilbert index of the box's 4x4x4-box brick over the
+ * simulation's brick grid (bits = ceil(log2) of its longest side), then by the
+ * Morton code of the box inside the brick.  Both stable (storage index). */
+int orc_curve_order(const orc_state *st, const orc_params *P, int64_t *perm) {
+  if (P->curve != 1) return orc_morton_order(st, P, perm);
+  int rc = check_state(st, P);
+  if (rc) return rc;
+  grid_t G;
+  rc = grid_build(st, P, &G);
+  if (rc) return rc;
+  sort_rec *r = (sort_rec *)malloc(sizeof(sort_rec) * (size_t)(st->n > 0 ? st->n : 1));
+  if (!r) { grid_free(&G); return ORC_ENOMEM; }
+  for (int64_t i = 0; i < st->n; ++i) {
+    const sim_grid *g = &G.g[G.sim_of[i]];
+    int64_t longest = 1;
+    for (int d = 0; d < 3; ++d) {
+      const int64_t bricks = (g->nb[d] + 3) / 4;
+      if (bricks > longest) longest = bricks;
+    }
+    int bits = 0;
+    while ((1LL << bits) < longest) ++bits;
+    const uint64_t h = orc_hilbert3((uint64_t)(G.bx[i] >> 2), (uint64_t)(G.by[i] >> 2), (uint64_t)(G.bz[i] >> 2), bits);
+    r[i].sim = G.sim_of[i];
+    r[i].code = (h << 6) | orc_morton3((uint64_t)(G.bx[i] & 3), (uint64_t)(G.by[i] & 3), (uint64_t)(G.bz[i] & 3));
+    r[i].idx = i;
+  }
+  qsort(r, (size_t)st->n, sizeof(sort_rec), cmp_sort_rec);
+  for (int64_t k = 0; k < st->n; ++k) perm[k] = r[k].idx;
+  free(r);
+  grid_free(&G);
+  return ORC_OK;
+}
+
 static int apply_sort(orc_state *st, const orc_params *P) {
   int64_t n = st->n;
   if (n <= 0) return ORC_OK;
   int64_t *perm = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
   double *tmp = (double *)malloc(sizeof(double) * (size_t)n);
   if (!perm || !tmp) { free(perm); free(tmp); return ORC_ENOMEM; }
-  int rc = orc_morton_order(st, P, perm);
+  int rc = orc_curve_order(st, P, perm);
   if (rc) { free(perm); free(tmp); return rc; }
   permute_f64(st->x, perm, n, tmp);
   permute_f64(st->y, perm, n, tmp);

@@ -51,7 +51,7 @@ class Params(C.Structure):
         ("detect_static", C.c_int32), ("sort_every", C.c_int32),
         ("growth", C.c_double), ("divide_volume", C.c_double),
         ("ratio_lo", C.c_double), ("ratio_hi", C.c_double), ("walk_step", C.c_double),
-        ("seed", C.c_uint64), ("death_prob", C.c_double), ("n_types", C.c_int32), ("pad", C.c_int32),
+        ("seed", C.c_uint64), ("death_prob", C.c_double), ("n_types", C.c_int32), ("curve", C.c_int32),
         ("type_k", C.c_double * 16), ("type_gamma", C.c_double * 16),
     ]
 
@@ -107,6 +107,10 @@ def _declare(L):
     L.orc_morton2.restype = C.c_uint64
     L.orc_threads.argtypes = []
     L.orc_threads.restype = C.c_int
+    L.orc_curve_order.argtypes = [SP, PP, vp]
+    L.orc_curve_order.restype = C.c_int
+    L.orc_hilbert3.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_int]
+    L.orc_hilbert3.restype = C.c_uint64
     L.orc_remove.argtypes = [SP, vp]
     L.orc_remove.restype = C.c_int64
     L.orc_morton_offsets.argtypes = [C.c_int32, vp, vp, vp, C.c_int64]
@@ -115,7 +119,7 @@ def _declare(L):
 
 DEFAULTS = dict(R=12.0, L=0.0, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.0,
                 detect_static=0, sort_every=0, growth=0.0, divide_volume=0.0,
-                ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, seed=0, death_prob=0.0)
+                ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, seed=0, death_prob=0.0, curve=0)
 
 
 def make_params(**kw) -> Params:
@@ -256,6 +260,15 @@ class State:
             raise RuntimeError("orc_morton_order failed: %d" % rc)
         return perm[: self.n]
 
+    def curve_order(self, params: Params):
+        """Storage order of a sort step for params.curve (0 Morton, 1 Hilbert
+        over the 4x4x4-box bricks, Morton inside a brick)."""
+        perm = np.zeros(max(self.n, 1), np.int64)
+        rc = lib().orc_curve_order(C.byref(self._s), C.byref(params), _ptr(perm))
+        if rc != 0:
+            raise RuntimeError("orc_curve_order failed: %d" % rc)
+        return perm[: self.n]
+
     def _csr(self, fn, params):
         n = self.n
         off = np.zeros(n + 1, np.int64)
@@ -322,6 +335,10 @@ def uniform(seed, uid, step, purpose):
 
 def morton3(x, y, z):
     return int(lib().orc_morton3(x, y, z))
+
+
+def hilbert3(x, y, z, bits):
+    return int(lib().orc_hilbert3(x, y, z, bits))
 
 
 def morton2(x, y):

@@ -39,6 +39,10 @@ MUTANTS = {
                                  "4u * TYPE_OF(st->beh[i]) + TYPE_OF(st->beh[i])"),
     "type_gamma_from_k_table": ("gamma = P->type_gamma[ab];", "gamma = P->type_k[ab];"),
     "type_bits_shifted": ("#define TYPE_OF(beh) (((beh) >> 4) & 3u)", "#define TYPE_OF(beh) (((beh) >> 3) & 3u)"),
+    "hilbert_no_reflection": ("X[0] ^= P; /* reflect the lower bits of axis 0 */", "(void)P;"),
+    "hilbert_no_exchange": ("        X[i] ^= t;\n      }", "      }"),
+    "hilbert_no_final_flip": ("  for (int i = 0; i < 3; ++i) X[i] ^= t;\n  uint64_t h = 0;", "  uint64_t h = 0;"),
+    "hilbert_gray_order": ("  X[1] ^= X[0]; /* Gray encode */\n  X[2] ^= X[1];", "  X[2] ^= X[1]; /* Gray encode */\n  X[1] ^= X[0];"),
 }
 
 
@@ -54,6 +58,8 @@ def _checks():
         c.append(lambda seed=seed: pins.test_parallel_removal_invariants(seed))
     for row in pins._hetero_lines():
         c.append(lambda row=row: pins.test_heterotypic_two_spheres_hand_worked(*row))
+    for bits in (2, 3):
+        c.append(lambda bits=bits: pins.test_hilbert_is_a_face_adjacent_bijection(bits))
     for kind in ("uniform", "lattice_ties", "clustered"):
         c.append(lambda kind=kind: pins.test_grid_neighbors_equal_brute_force(kind))
     for key, ctr in [((5, 7), (0, 0, 0, 0)), ((2**64 - 1, 123), (2**64 - 1, 3, 9, 1))]:
