@@ -63,6 +63,8 @@ def parse():
                     help="blobs is the headline; the others measure the remaining configurations")
     ap.add_argument("--sort-every", type=int, default=10,
                     help="blobs: Morton re-sort cadence (0 = never; the headline workload uses 10)")
+    ap.add_argument("--curve", default="morton", choices=["morton", "hilbert"],
+                    help="blobs: space-filling curve of the sort (bricks of 4x4x4 boxes along it)")
     ap.add_argument("--presort", action="store_true",
                     help="blobs: put storage in Morton order (bdm_sort) before the warm-up")
     ap.add_argument("--no-autotune", action="store_true", help="ensemble, core_shell: skip the autotuner")
@@ -83,11 +85,13 @@ def workload(n):
 def config(args):
     return {
         "workload": "blobs-%d: 8 Gaussian blobs (sigma 150 um) in [0,4000]^3 um, diameters U[9,11] um, "
-                    "R = L = 11 um, dt 0.01, max displacement 3 um, Morton re-sort every 10 iterations" % args.n,
+                    "R = L = 11 um, dt 0.01, max displacement 3 um, %s re-sort every %d iterations" % (
+                        args.n, args.curve.capitalize(), args.sort_every),
         "n_agents": args.n,
         "precision": "FP32 pair force and accumulation; FP64 cutoff predicate, contact decision and positions",
         "l2_policy": "inputs larger than L2 (about 1 GB touched per iteration vs 129 MB L2); no flush",
         "sort_every": args.sort_every,
+        "curve": args.curve,
         "presort": bool(args.presort),
         "parallelism": "replica per GPU" if args.gpus > 1 else "single GPU",
     }
@@ -508,7 +512,8 @@ def main():
 
     w = workload(args.n)
     stream = torch.cuda.current_stream()
-    sim = bdm.Simulation.from_workload(w, precision="fp32", sort_every=args.sort_every)
+    curve = bdm.CURVE_HILBERT if args.curve == "hilbert" else bdm.CURVE_MORTON
+    sim = bdm.Simulation.from_workload(w, precision="fp32", sort_every=args.sort_every, curve=curve)
     sim.set_workload(w)
     if args.presort:
         sim.sort()

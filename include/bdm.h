@@ -58,6 +58,10 @@ extern "C" {
 #define BDM_FP32_FORCE 1 /* FP32 pair arithmetic and accumulation; FP64 cutoff predicate,
                             FP64 contact decision and FP64 positions; diameters in FP32  */
 
+/* space-filling curves of the agent order */
+#define BDM_CURVE_MORTON 0
+#define BDM_CURVE_HILBERT 1
+
 /* memory tags */
 #define BDM_HOST 0
 #define BDM_DEVICE 1
@@ -97,7 +101,10 @@ typedef struct {
                                 type_gamma[4 a + b] (Sec. 6.5 cell sorting:
                                 differential adhesion); the type is bits 4-5 of
                                 the agent's behaviour byte (BDM_TYPE_SHIFT)          */
-  int32_t reserved2;
+  int32_t curve;             /* order of the grid and of sort steps (Sec. 4.2):
+                                BDM_CURVE_MORTON (0) or BDM_CURVE_HILBERT (1): the
+                                4x4x4-box bricks along a Hilbert curve, the boxes
+                                inside a brick in Morton order                      */
   double type_k[16];         /* symmetric, finite, >= 0 over the first n_types rows;
                                 entries of types >= n_types are used as given       */
   double type_gamma[16];

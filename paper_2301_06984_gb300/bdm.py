@@ -15,6 +15,7 @@ from . import build as _build
 BDM_OK, BDM_EINVAL, BDM_ENOMEM, BDM_ECUDA, BDM_ECAPACITY, BDM_ETIMEOUT, BDM_ESTATE = 0, -1, -2, -3, -4, -5, -6
 BDM_FP64, BDM_FP32_FORCE = 0, 1
 BDM_HOST, BDM_DEVICE = 0, 1
+CURVE_MORTON, CURVE_HILBERT = 0, 1
 BEH_GROW, BEH_WALK, BEH_DIE = 1, 2, 4
 TYPE_SHIFT = 4  # bits 4-5 of the behaviour byte: the agent's type
 DBG_FORCES, DBG_NZ, DBG_STATIC, DBG_GRID_BOX, DBG_GRID_ORDER = 1, 2, 3, 4, 5
@@ -39,7 +40,7 @@ class Params(C.Structure):
         ("growth_per_step", C.c_double), ("divide_volume", C.c_double), ("ratio_lo", C.c_double),
         ("ratio_hi", C.c_double), ("walk_step", C.c_double), ("capacity", C.c_int64),
         ("keep_forces", C.c_int32), ("reserved", C.c_int32), ("death_prob", C.c_double),
-        ("n_types", C.c_int32), ("reserved2", C.c_int32), ("type_k", C.c_double * 16),
+        ("n_types", C.c_int32), ("curve", C.c_int32), ("type_k", C.c_double * 16),
         ("type_gamma", C.c_double * 16),
     ]
 
@@ -133,7 +134,7 @@ class Simulation:
     def __init__(self, R, capacity, box_edge=0.0, dt=0.01, dmax=3.0, k=2.0, gamma=1.0, adherence=0.0,
                  precision="fp64", detect_static=False, sort_every=0, n_sims=1, dt_per_sim=None, seed=0,
                  growth=0.0, divide_volume=0.0, ratio_lo=0.9, ratio_hi=1.1, walk_step=0.0, keep_forces=False,
-                 death_prob=0.0, type_k=None, type_gamma=None, stream=None):
+                 death_prob=0.0, type_k=None, type_gamma=None, curve=0, stream=None):
         L = lib()
         p = Params()
         p.interaction_radius = R
@@ -160,6 +161,7 @@ class Simulation:
         p.capacity = int(capacity)
         p.keep_forces = int(bool(keep_forces))
         p.death_prob = death_prob
+        p.curve = int(curve)
         if type_k is not None:
             tk, tg = np.asarray(type_k, np.float64), np.asarray(type_gamma, np.float64)
             p.n_types = tk.shape[0]
@@ -197,7 +199,7 @@ class Simulation:
                   seed=p.get("seed", 0), growth=p.get("growth", 0.0), divide_volume=p.get("divide_volume", 0.0),
                   ratio_lo=p.get("ratio_lo", 0.9), ratio_hi=p.get("ratio_hi", 1.1),
                   walk_step=p.get("walk_step", 0.0), death_prob=p.get("death_prob", 0.0),
-                  type_k=p.get("type_k"), type_gamma=p.get("type_gamma"))
+                  type_k=p.get("type_k"), type_gamma=p.get("type_gamma"), curve=p.get("curve", 0))
         kw.update(over)
         return cls(capacity=capacity or w.n, **kw)
 

@@ -130,14 +130,13 @@ struct DevParams {
   float rel_tol, abs_tol;           // FP32-form force tolerance the refinement keeps
   float low_scale;                  // agents whose summed pair-force magnitude is below this
                                     // are evaluated in FP64
-  float close2;                     // FP32 form, fix-up pass: pairs closer than this (um^2)
-                                    // are evaluated in FP64
-  float dir_e;                      // bound of the FP32 error of a coordinate difference
-                                    // (times sqrt 3): the direction error of a pair is dir_e / d
+  float close2;                     // FP32 form: pairs closer than this (um^2) are evaluated
+                                    // in FP64 (their FP32 direction is too rough)
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk, die;
   int32_t n_types;                  // > 1: the pair's constants are type_k / type_gamma[4 a + b]
+  int32_t curve;                    // brick order: 0 Morton, 1 Hilbert
   double type_k[16], type_gamma[16];  // of the agents' types a, b (bits 4-5 of the behaviour)
   int32_t lanes_fixed;              // FP32 form: > 0 lanes per agent of the force kernel; -1
                                     // lanes chosen per box by its cost model

@@ -423,6 +423,8 @@ int bdm_create(const bdm_params *params, void *stream, bdm_sim **out) {
   if (!(P.death_prob >= 0.0 && P.death_prob <= 1.0)) return fail(nullptr, BDM_EINVAL, "death_prob must be in [0, 1]");
   if (P.death_prob > 0.0 && P.n_sims > 1) return fail(nullptr, BDM_EINVAL, "removal needs n_sims == 1");
   if (P.n_types < 0 || P.n_types > 4) return fail(nullptr, BDM_EINVAL, "n_types must be in [0, 4]");
+  if (P.curve != BDM_CURVE_MORTON && P.curve != BDM_CURVE_HILBERT)
+    return fail(nullptr, BDM_EINVAL, "curve must be BDM_CURVE_MORTON or BDM_CURVE_HILBERT");
   for (int a = 0; a < P.n_types && P.n_types > 1; ++a)
     for (int b = 0; b < P.n_types; ++b) {
       const double k = P.type_k[4 * a + b], g = P.type_gamma[4 * a + b];

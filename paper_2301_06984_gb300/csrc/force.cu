@@ -222,7 +222,6 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 
 #define FORCE_WARPS 8
 #define CHUNK 96
-#define RISK_SLOTS 2  // risky contacts a lane records for the FP64 replay
 
 // Next occupied brick for a force-kernel CTA (called by one thread; phase is
 // that thread's cursor, starting at 0): the heaviest bricks first, so that no
@@ -448,11 +447,51 @@ __device__ __forceinline__ unsigned scan_chunk(const float4 *sc, uint8_t *q, con
   return (unsigned)(q - q0) >> 5;
 }
 
+// Force of a certain contact from the exact geometry, for the FP32 form's
+// contacts whose box-local FP32 records are too coarse (grazing contacts,
+// forces near the sign change of k delta - gamma sqrt(rbar delta), close
+// pairs).  The two FP64 positions are converted to the grid's fixed point (the
+// truncation of each coordinate is below 2^-fs um), so the difference D and
+// N = S^2 - |D|^2 (S = r_i + r_j, radii exact in the fixed point) are exact
+// integers; delta = N / (S + d) then carries only the FP32 rounding of the
+// quotient (about 3e-7 relative) and the direction D / d that of d, all
+// without the FP64 pipe.  pq and pc: x, y, z in FP64 and the radius in w.
+// Returns the force vector on the agent at pq and |F|.
+__device__ __forceinline__ float contact_int(const dbl4 &pq, const dbl4 &pc, int fs, float k, float gamma, float &fx,
+                                             float &fy, float &fz) {
+  const long long dx = to_fixed(pq.x, fs) - to_fixed(pc.x, fs);
+  const long long dy = to_fixed(pq.y, fs) - to_fixed(pc.y, fs);
+  const long long dz = to_fixed(pq.z, fs) - to_fixed(pc.z, fs);
+  const long long D2 = dx * dx + dy * dy + dz * dz;  // |D| < 2^30: no overflow
+  const float rq = (float)pq.w, rc = (float)pc.w;     // exact: the radii are floats
+  const float scale = __int_as_float((127 + fs) << 23), unscale = __int_as_float((127 - fs) << 23);
+  const long long S = (long long)__fmul_rn(rq, scale) + (long long)__fmul_rn(rc, scale);
+  const long long N = S * S - D2;
+  fx = fy = fz = 0.f;
+  if (D2 <= 0 || N <= 0) return 0.f;
+  const float d = sqrtf((float)D2);
+  const float delta = __fmul_rn(__fdiv_rn((float)N, __fadd_rn((float)S, d)), unscale);
+  const float rbar = __fdiv_rn(__fmul_rn(rq, rc), __fadd_rn(rq, rc));
+  const float F = fmaf(k, delta, -__fmul_rn(gamma, sqrtf(__fmul_rn(rbar, delta))));
+  const float sc = __fdiv_rn(F, d);
+  fx = __fmul_rn(sc, (float)dx);
+  fy = __fmul_rn(sc, (float)dy);
+  fz = __fmul_rn(sc, (float)dz);
+  return fabsf(F);
+}
+
+// The same, out of line (for the force kernel's rare use, so that its main
+// loop keeps its registers).
+__device__ __noinline__ float contact_int_call(const dbl4 &pq, const dbl4 &pc, int fs, float k, float gamma, float &fx,
+                                               float &fy, float &fz) {
+  return contact_int(pq, pc, fs, k, gamma, fx, fy, fz);
+}
+
 // FP32 force of a certain contact at squared distance d2 (s = r_i + r_j, pi =
 // r_i r_j): overlap delta, the scale F / d of the difference vector, and the
 // force F itself.  Every operation is rounded as written (the fused
-// multiply-adds are explicit), so the force kernel and the FP64 replay form
-// the same bits.
+// multiply-adds are explicit), so the force kernel and the FP64 fix-up pass
+// form the same bits for the contacts both evaluate in FP32.
 struct ContactF32 {
   float inv_d, delta, rbar, sq, fm, scf;
 };
@@ -468,49 +507,11 @@ __device__ __forceinline__ ContactF32 contact_f32(float d2, float s, float pi, f
   return c;
 }
 
-// FP64 replay of a lane's recorded risky contacts (FP32 form): for each, the
-// FP64 contribution minus the FP32 contribution the force kernel added for it
-// (recomputed with the same FP32 operations from the same staged record:
-// box-local coordinates plus the offset of its stencil box, found among the
-// warp's 27 box ranges pre/st), summed into d*.  Out of line, so that the
-// force kernel's main loop keeps its registers.
-__device__ __noinline__ void replay_risky(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur, unsigned kq,
-                                          float4 cq, int tq4, unsigned nrisk, const uint32_t *rk, const unsigned *pre,
-                                          const unsigned *st, const float4 *off, const double *tkd, const double *tgd,
-                                          const float *tkf, const float *tgf, float &dx, float &dy, float &dz,
-                                          unsigned &n_exact) {
-  const dbl4 pq = exact_of<1>(B, A, cur, kq);
-  double hx = 0.0, hy = 0.0, hz = 0.0;
-  float fx = 0.f, fy = 0.f, fz = 0.f;
-  for (unsigned r = 0; r < nrisk; ++r) {
-    const unsigned kj = rk[32 * r];
-    int bx = 0;
-    for (int b = 0; b < 27; ++b)
-      if (kj - st[b] < pre[b + 1] - pre[b]) bx = b;  // kj in box b's range (unsigned wrap excludes below)
-    const float4 of = off[bx];
-    const float4 c0 = B.c32[kj];
-    const float4 c = make_float4(c0.x + of.x, c0.y + of.y, c0.z + of.z, c0.w);
-    const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
-    // the force kernel's FP32 contribution of this (certain, FP32) contact
-    const float2 e = sub_xy(cq, c);
-    const float ez = cq.z - c.z;
-    const float d2 = fmaf(e.x, e.x, fmaf(e.y, e.y, __fmul_rn(ez, ez)));
-    const ContactF32 k = contact_f32(d2, __fadd_rn(cq.w, c.w), __fmul_rn(cq.w, c.w), tkf[ab], tgf[ab]);
-    fx = fmaf(k.scf, e.x, fx);
-    fy = fmaf(k.scf, e.y, fy);
-    fz = fmaf(k.scf, ez, fz);
-    atomicAdd(&n_exact, 1u);
-    pair_f64_k(P.R2, tkd[ab], tgd[ab], pq, exact_of<1>(B, A, cur, kj), hx, hy, hz);
-  }
-  dx = (float)(hx - (double)fx);
-  dy = (float)(hy - (double)fy);
-  dz = (float)(hz - (double)fz);
-}
-
 // SPLIT (FP32 step without random walk or growth only): the agent's lanes
 // finish one axis each.  A separate instantiation, so that the other forms
 // keep the register allocation they have without that code.
-template <int PREC, int MODE, bool SPLIT = false>
+// TYPES: several agent types (the pair constants from the type tables).
+template <int PREC, int MODE, bool SPLIT = false, bool TYPES = false>
 __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevParams P) {
   static_assert(!SPLIT || (PREC == 1 && MODE == FM_STEP), "the split epilogue is the FP32 step's");
   __shared__ int s_nocc[27];
@@ -535,8 +536,6 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ unsigned s_pre[FORCE_WARPS][28], s_st[FORCE_WARPS][28];
   // several agent types: the staged candidates' types and the pair constants
   __shared__ uint8_t s_tp[FORCE_WARPS][CHUNK];
-  // FP32 form: per lane, the sorted indices of its first risky contacts
-  __shared__ uint32_t s_rk[FORCE_WARPS][RISK_SLOTS][32];
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
   DevCounters *C = B.ctr;
@@ -556,7 +555,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   }
   if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
   if (lane < 4) s_ctr[warp][lane] = 0u;
-  if (threadIdx.x < 16) {
+  if (TYPES && threadIdx.x < 16) {
     s_tkd[threadIdx.x] = P.type_k[threadIdx.x];
     s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
     s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
@@ -675,7 +674,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         if (PREC == 0) dq = B.c64[kq];
         const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
         const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
-        const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;  // the agent's row of the type tables
+        const int tq4 = TYPES ? 4 * (int)B.tp[kq] : 0;  // the agent's row of the type tables
         if (SPLIT && S >= 4 && valid && !is_static && sub < 3) {
           // this lane's axis of the agent's position, copied to shared memory
           // while the pairs are evaluated (waited for in the epilogue)
@@ -691,7 +690,6 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           if (lane == 0) s_ctr[warp][0] += ctot * (na / (unsigned)S);
         }
         float ffx = 0.f, ffy = 0.f, ffz = 0.f, gbound = 0.f, fscale = 0.f;
-        unsigned nrisk = 0;  // FP32 form: risky contacts (the first ones' indices in s_rk)
         double dfx = 0.0, dfy = 0.0, dfz = 0.0;
         unsigned ncont = 0, nnb = 0;
         long long lbase = 0;
@@ -741,7 +739,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   const float4 of = s_off[boxs[m]];
                   sc[t] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
                   skj[t] = kjs[m];
-                  if (P.n_types > 1) s_tp[warp][t] = B.tp[kjs[m]];
+                  if (TYPES) s_tp[warp][t] = B.tp[kjs[m]];
                 }
               }
               c0 += fill;
@@ -789,7 +787,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                     const unsigned kj = skj[s_q[warp][e - qs[ow]][ow]];
                     const unsigned ko = kqs[ow];
                     double kk = P.k, gg = P.gamma;
-                    if (P.n_types > 1) {
+                    if (TYPES) {
                       const int ab = 4 * (int)B.tp[ko] + (int)B.tp[kj];
                       kk = s_tkd[ab];
                       gg = s_tgd[ab];
@@ -833,8 +831,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                     }
                     continue;
                   }
-                  const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
-                  const int r = pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, cj, dfx, dfy, dfz);
+                  const int ab = tq4 + (TYPES ? (int)B.tp[kj] : 0);
+                  const int r = pair_f64_k(P.R2, TYPES ? s_tkd[ab] : P.k, TYPES ? s_tgd[ab] : P.gamma, dq, cj, dfx,
+                                           dfy, dfz);
                   nnb += (r > 0);
                   ncont += (r == 2);
                   continue;
@@ -857,7 +856,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 }
                 const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
                 const float W = fmaf(s, P.cband1, s2 * P.cband2);
-                const int ab = tq4 + ((P.n_types > 1) ? (int)s_tp[warp][i] : 0);
+                const int ab = tq4 + (TYPES ? (int)s_tp[warp][i] : 0);
+                const float kf = TYPES ? s_tkf[ab] : P.kf, gf = TYPES ? s_tgf[ab] : P.gammaf;
                 bool exact = band || (d2 > s2 - W && d2 < s2 + W);  // cutoff or contact decided in FP64
                 ContactF32 k = {};
                 if (!exact) {
@@ -865,16 +865,27 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                     nnb++;
                     continue;
                   }
-                  k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
-                  // a contact so shallow that gamma sqrt(rbar delta) is too steep
-                  // for the FP32 overlap: in FP64 as well
-                  exact = k.delta < P.graze_exact;
+                  k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), kf, gf);
+                  // from the exact geometry instead: a contact so shallow that
+                  // gamma sqrt(rbar delta) is too steep for the FP32 overlap, or
+                  // a pair so close that the FP32 rounding of its difference
+                  // vector turns its direction too much
+                  if (k.delta < P.graze_exact || d2 < P.close2) {
+                    atomicAdd(&s_ctr[warp][3], 1u);
+                    float tx, ty, tz;
+                    fscale += contact_int(exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), P.fix_shift, kf,
+                                          gf, tx, ty, tz);
+                    ffx += tx; ffy += ty; ffz += tz;
+                    nnb++;
+                    ncont++;
+                    continue;
+                  }
                 }
                 if (exact) {
                   atomicAdd(&s_ctr[warp][3], 1u);
                   double gx = 0.0, gy = 0.0, gz = 0.0;
-                  const int r = pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], exact_of<1>(B, A, cur, kq),
-                                           exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                  const int r = pair_f64_k(P.R2, TYPES ? s_tkd[ab] : P.k, TYPES ? s_tgd[ab] : P.gamma,
+                                           exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
                   nnb += (r > 0);
                   if (r == 2) {
                     ncont++;
@@ -885,21 +896,12 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   continue;
                 }
                 nnb++;
-                const float gf = s_tgf[ab], delta = k.delta, rbar = k.rbar, sq = k.sq, fm = k.fm, scf = k.scf;
-                // a contact whose FP32 error is not negligible against a small
-                // tolerance (grazing, near the sign change of the force, or a
-                // close pair): summed apart, its index kept for an FP64 replay
-                if (delta < P.graze || fabsf(fm) < P.low_scale || d2 < P.close2) {
-                  if (nrisk < RISK_SLOTS) s_rk[warp][nrisk][lane] = kj;
-                  nrisk++;
-                }
+                const float delta = k.delta, rbar = k.rbar, sq = k.sq, fm = k.fm, scf = k.scf;
                 ffx = fmaf(scf, ex, ffx);
                 ffy = fmaf(scf, ey, ffy);
                 ffz = fmaf(scf, ez, ffz);
-                // error bound: the direction (p_i - p_j) / d carries the
-                // coordinates' rounding over d (large for close pairs), and
-                // a grazing contact's sqrt(rbar delta) is steep in delta
-                gbound = fmaf(fabsf(scf), P.dir_e, gbound);
+                // error bound of a grazing contact: sqrt(rbar delta) is steep
+                // in delta
                 if (delta < P.graze)
                   gbound += (sq > 1e-18f) ? fminf(gf * rbar * P.graze_e * 0.5f * __frcp_rn(sq),
                                                   gf * sqrtf(rbar * P.graze_e))
@@ -924,35 +926,16 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           }
         }
         // FP32 form: the agent's tolerance is rel_tol * S + abs_tol, S =
-        // fscale, the sum of its pair-force magnitudes.  When the FP32 error
-        // bound is not a small part of it, or S is so small that the absolute
-        // floor dominates (S < low_scale: the coordinates' rounding, about
-        // 1e-6 um per contact, is no longer negligible), the agent's risky
-        // contacts are replayed in FP64 here (their FP32 sum replaced), or,
-        // when a lane had more of them than it could record, the agent goes to
-        // the FP64 fix-up pass, which evaluates and finishes it.
+        // fscale, the sum of its pair-force magnitudes.  When the bound of its
+        // grazing contacts' FP32 error is not a small part of it, or S is so
+        // small that the absolute floor dominates (S < low_scale: the
+        // coordinates' rounding, about 1e-6 um per contact, is no longer
+        // negligible), the agent goes to the FP64 fix-up pass, which
+        // evaluates and finishes it.
         bool need_fix = false;
         if (PREC == 1 && (MODE == FM_STEP || MODE == FM_FORCES)) {
-          const bool flagged = compute && ncont > 0 &&
-                               (fscale < P.low_scale || gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol));
-          unsigned over = (nrisk > RISK_SLOTS) ? 1u : 0u;
-          for (int of = S >> 1; of > 0; of >>= 1) over |= __shfl_xor_sync(0xffffffffu, over, of);
-          const bool replay = flagged && !over;
-          need_fix = flagged && over;
-          if (__any_sync(0xffffffffu, replay)) {
-            // each lane: sum over its recorded contacts of (FP64 contribution
-            // - the FP32 contribution it added above, recomputed by the same
-            // arithmetic), so that the FP64 values replace the FP32 ones
-            float dx = 0.f, dy = 0.f, dz = 0.f;
-            if (replay) replay_risky(B, P, A, cur, kq, cq, tq4, nrisk, &s_rk[warp][0][lane], s_pre[warp], s_st[warp],
-                                     s_off, s_tkd, s_tgd, s_tkf, s_tgf, dx, dy, dz, s_ctr[warp][3]);
-            for (int of = S >> 1; of > 0; of >>= 1) {
-              dx += __shfl_xor_sync(0xffffffffu, dx, of);
-              dy += __shfl_xor_sync(0xffffffffu, dy, of);
-              dz += __shfl_xor_sync(0xffffffffu, dz, of);
-            }
-            if (replay) { ffx += dx; ffy += dy; ffz += dz; }
-          }
+          need_fix = compute && ncont > 0 &&
+                     (fscale < P.low_scale || gbound > 0.25f * (P.rel_tol * fscale + P.abs_tol));
           if (need_fix && sub == 0) {
             const unsigned long long e = atomicAdd(&C->fix_n, 1ull);
             if (BDM_IN(B.ctr, (long long)e < B.cap)) B.fix[e] = make_uint4(kq, (uint32_t)(o * 64 + lb), ncont, nnb);
@@ -1141,18 +1124,21 @@ __global__ void k_reset_work(DevBufs B) {
 // The FP32-form agents that the force kernel listed (an FP32 error bound not
 // small against the agent's tolerance, or a summed pair-force magnitude so
 // small that the absolute floor dominates) are evaluated again here, one warp
-// per agent: the lanes take strides of the agent's 27-box stencil.  Every
-// contact the FP32 error analysis does not cover -- one the FP32 bands cannot
-// decide, a grazing contact (delta < graze), a contact whose force magnitude
-// is below low_scale (near the sign change of k delta - gamma sqrt(rbar
-// delta), where rounding is large against the force) and a close pair
-// (d^2 < close2, whose direction carries the coordinates' rounding over d) --
-// is evaluated in FP64; the other contacts exactly as the force kernel does.
+// per agent: the lanes walk the agent's 27-box stencil.  A pair the FP32
+// bands cannot decide (cutoff or contact) and a contact whose force magnitude
+// is below low_scale (near the sign change of k delta - gamma sqrt(rbar delta))
+// go to the warp's list of FP64 pairs; a grazing contact (delta < graze) and a
+// close pair (d^2 < close2) take the exact-integer geometry of contact_int; the
+// other
+// contacts are summed exactly as the force kernel does.  The list is evaluated
+// in FP64 32 pairs per warp instruction (an FP64 instruction costs GB300's slow
+// FP64 pipe as much for one active lane as for 32) and summed in list order.
 // The sum, rounded to FP32, goes through the force kernel's epilogue
 // (displacement, behaviours, flags, bounding box), or to the debug outputs in
 // FM_FORCES; the neighbour and contact counts are the force kernel's.
 #define FIX_WARPS 8
-#define FIX_BATCH 4
+#define FIX_BATCH 4   // candidates per lane whose loads are in flight together
+#define FIX_PAIRS 64  // FP64 pairs a warp's list holds (evaluated when full)
 template <int MODE>
 __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevParams P) {
   __shared__ unsigned s_pre[FIX_WARPS][28], s_st[FIX_WARPS][28];
@@ -1162,6 +1148,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
   __shared__ float4 s_fc[FIX_WARPS][FIX_BATCH][32];
   __shared__ unsigned s_fk[FIX_WARPS][FIX_BATCH][32];
   __shared__ uint8_t s_fb[FIX_WARPS][FIX_BATCH][32];
+  __shared__ unsigned s_pk[FIX_WARPS][FIX_PAIRS];  // the list: candidates' sorted indices
   DevCounters *C = B.ctr;
   if (C->error) return;
   const unsigned long long nfix = C->fix_n;
@@ -1181,14 +1168,15 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
   __syncwarp();
   unsigned c_static = 0, c_moved = 0, n_exact = 0;
   int wsim = -1;
+  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
   for (unsigned long long e = (unsigned long long)blockIdx.x * FIX_WARPS + warp; e < nfix;
        e += (unsigned long long)gridDim.x * FIX_WARPS) {
     if (!BDM_IN(B.ctr, (long long)e < B.cap)) break;
     const uint4 ent = B.fix[e];
     const unsigned kq = ent.x;
     const long long o = (long long)(ent.y >> 6);
-    if (!BDM_IN(B.ctr, o < C->n_occ && (long long)kq < C->n)) continue;
     const int lb = (int)(ent.y & 63u);
+    if (!BDM_IN(B.ctr, o < C->n_occ && (long long)kq < C->n)) continue;
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
     if (MODE == FM_STEP && info.w != wsim) {
@@ -1228,18 +1216,32 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
     const float4 cq = B.c32[kq];
     const dbl4 dq = exact_of<1>(B, A, cur, kq);
     const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;
-    double fx = 0.0, fy = 0.0, fz = 0.0;
-    float gx = 0.f, gy = 0.f, gz = 0.f;
-    for (unsigned p0 = lane; p0 < ctot; p0 += 32u * FIX_BATCH) {
+    double hx = 0.0, hy = 0.0, hz = 0.0;  // this lane's FP64 pairs
+    float gx = 0.f, gy = 0.f, gz = 0.f;   // this lane's FP32 contacts
+    unsigned np = 0;                      // pairs in the list (warp-uniform)
+    // evaluate the listed FP64 pairs, 32 per warp instruction
+    auto flush_pairs = [&]() {
+      for (unsigned p0 = 0; p0 < np; p0 += 32) {
+        if (p0 + lane < np) {
+          const unsigned kj = s_pk[warp][p0 + lane];
+          const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
+          pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, exact_of<1>(B, A, cur, kj), hx, hy, hz);
+          n_exact++;
+        }
+      }
+      np = 0;
+      __syncwarp();
+    };
+    for (unsigned p0 = 0; p0 < ctot; p0 += 32u * FIX_BATCH) {
       // FIX_BATCH candidates per lane: their loads in flight together, the
-      // records kept in shared memory for the evaluation loop
+      // records kept in shared memory for the classification loop
       {
         unsigned kjv[FIX_BATCH];
         int bxv[FIX_BATCH];
         float4 cv[FIX_BATCH];
 #pragma unroll
         for (int u = 0; u < FIX_BATCH; ++u) {
-          const unsigned p = p0 + 32u * u;
+          const unsigned p = p0 + lane + 32u * u;
           int bx = 0;
           for (int st = 16; st > 0; st >>= 1)
             if (bx + st <= 26 && s_pre[warp][bx + st] <= p) bx += st;
@@ -1248,7 +1250,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
         }
 #pragma unroll
         for (int u = 0; u < FIX_BATCH; ++u)
-          if (p0 + 32u * u < ctot) cv[u] = __ldg(&B.c32[kjv[u]]);
+          if (p0 + lane + 32u * u < ctot) cv[u] = __ldg(&B.c32[kjv[u]]);
 #pragma unroll
         for (int u = 0; u < FIX_BATCH; ++u) {
           s_fc[warp][u][lane] = cv[u];
@@ -1257,59 +1259,79 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
         }
       }
       for (int u = 0; u < FIX_BATCH; ++u) {
-      if (p0 + 32u * u >= ctot) break;
-      const unsigned kj = s_fk[warp][u][lane];
-      const int bx = (int)s_fb[warp][u][lane];
-      if (kj == kq) continue;
-      if (!BDM_IN(B.ctr, (long long)kj < C->n)) continue;
-      const float4 c = s_fc[warp][u][lane];
-      const float ofx = (float)(bx % 3 - 1) * P.Lf, ofy = (float)((bx / 3) % 3 - 1) * P.Lf,
-                  ofz = (float)(bx / 9 - 1) * P.Lf;
-      const float ex = cq.x - (c.x + ofx), ey = cq.y - (c.y + ofy), ez = cq.z - (c.z + ofz);
-      const float d2 = fmaf(ex, ex, fmaf(ey, ey, ez * ez));
-      if (d2 >= P.R2_hi_f) continue;  // certainly no neighbour
-      const float s = cq.w + c.w, s2 = s * s;
-      const float W = fmaf(s, P.cband1, s2 * P.cband2);
-      const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
-      if (!band && d2 >= s2 + W) continue;  // certainly no contact
-      const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
-      bool exact = band || d2 > s2 - W || d2 < P.close2;
-      if (!exact) {
-        // a certain contact: the force kernel's FP32 arithmetic
-        const float inv_d = rsqrtf(d2);
-        const float delta = s - d2 * inv_d;
-        const float rbar = __fdividef(cq.w * c.w, s);
-        const float rd = rbar * delta;
-        const float sq = rd * rsqrtf(rd);
-        const float fm = s_tkf[ab] * delta - s_tgf[ab] * sq;
-        exact = delta < P.graze || fabsf(fm) < P.low_scale;
-        if (!exact) {
-          const float scf = fm * inv_d;
-          gx = fmaf(scf, ex, gx);
-          gy = fmaf(scf, ey, gy);
-          gz = fmaf(scf, ez, gz);
-          continue;
+        if (p0 + 32u * u >= ctot) break;  // warp-uniform
+        bool risky = false;
+        unsigned kj = 0;
+        if (p0 + lane + 32u * u < ctot) {
+          kj = s_fk[warp][u][lane];
+          const int bx = (int)s_fb[warp][u][lane];
+          const float4 c = s_fc[warp][u][lane];
+          if (kj != kq && BDM_IN(B.ctr, (long long)kj < C->n)) {
+            const float ofx = (float)(bx % 3 - 1) * P.Lf, ofy = (float)((bx / 3) % 3 - 1) * P.Lf,
+                        ofz = (float)(bx / 9 - 1) * P.Lf;
+            const float ex = __fsub_rn(cq.x, __fadd_rn(c.x, ofx)), ey = __fsub_rn(cq.y, __fadd_rn(c.y, ofy)),
+                        ez = __fsub_rn(cq.z, __fadd_rn(c.z, ofz));
+            const float d2 = fmaf(ex, ex, fmaf(ey, ey, __fmul_rn(ez, ez)));
+            if (d2 < P.R2_hi_f) {  // else certainly no neighbour
+              const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
+              const float W = fmaf(s, P.cband1, s2 * P.cband2);
+              const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+              if (band || d2 < s2 + W) {  // else a neighbour, certainly no contact
+                // the cutoff or the contact undecided in FP32: FP64 (list)
+                risky = band || d2 > s2 - W;
+                if (!risky) {
+                  // a certain contact: the force kernel's FP32 arithmetic, or
+                  // the exact-geometry path where that is too coarse; a force
+                  // magnitude below low_scale sits near the root of
+                  // k delta = gamma sqrt(rbar delta), where an FP32 delta's
+                  // rounding (k/2 * delta * eps) is not small against the
+                  // absolute floor: FP64 (list)
+                  const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
+                  const ContactF32 k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
+                  risky = fabsf(k.fm) < P.low_scale;
+                  if (!risky && (k.delta < P.graze || d2 < P.close2)) {
+                    float tx, ty, tz;
+                    contact_int(dq, exact_of<1>(B, A, cur, kj), P.fix_shift, s_tkf[ab], s_tgf[ab], tx, ty, tz);
+                    hx += (double)tx;
+                    hy += (double)ty;
+                    hz += (double)tz;
+                    n_exact++;
+                  } else if (!risky) {
+                    gx = fmaf(k.scf, ex, gx);
+                    gy = fmaf(k.scf, ey, gy);
+                    gz = fmaf(k.scf, ez, gz);
+                  }
+                }
+              }
+            }
+          }
         }
-      }
-      n_exact++;
-      pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, exact_of<1>(B, A, cur, kj), fx, fy, fz);
+        // append this step's FP64 pairs to the list (lane order), evaluating
+        // the list first when they would not fit
+        const unsigned bal = __ballot_sync(0xffffffffu, risky);
+        const unsigned cnt = __popc(bal);
+        if (np + cnt > FIX_PAIRS) flush_pairs();
+        if (risky) s_pk[warp][np + __popc(bal & lt)] = kj;
+        np += cnt;
+        __syncwarp();
       }
     }
-    fx += (double)gx;
-    fy += (double)gy;
-    fz += (double)gz;
+    flush_pairs();
+    hx += (double)gx;
+    hy += (double)gy;
+    hz += (double)gz;
     for (int of = 16; of > 0; of >>= 1) {
-      fx += __shfl_xor_sync(0xffffffffu, fx, of);
-      fy += __shfl_xor_sync(0xffffffffu, fy, of);
-      fz += __shfl_xor_sync(0xffffffffu, fz, of);
+      hx += __shfl_xor_sync(0xffffffffu, hx, of);
+      hy += __shfl_xor_sync(0xffffffffu, hy, of);
+      hz += __shfl_xor_sync(0xffffffffu, hz, of);
     }
-    const unsigned ncont = ent.z, nnb = ent.w;
     if (lane == 0) {
       const uint32_t iq = B.perm[kq];
       double px = 0.0, py = 0.0, pz = 0.0;
       if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
-      finish_agent<1, MODE>(B, P, A, cur, nxt, step, G.dt, G.dt_f, iq, A.flags[iq], false, (float)fx, (float)fy,
-                            (float)fz, 0.0, 0.0, 0.0, nnb, ncont, c_static, c_moved, s_bb[warp], px, py, pz);
+      // the force kernel's neighbour and contact counts (ent.w, ent.z)
+      finish_agent<1, MODE>(B, P, A, cur, nxt, step, G.dt, G.dt_f, iq, A.flags[iq], false, (float)hx, (float)hy,
+                            (float)hz, 0.0, 0.0, 0.0, ent.w, ent.z, c_static, c_moved, s_bb[warp], px, py, pz);
     }
     __syncwarp();
   }
@@ -1603,23 +1625,25 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
   k_reset_work<<<1, 1, 0, s>>>(B);
   if (mode == FM_STEP && P.detect_static) k_static<<<2 * c.occ_blocks, KS_WARPS * 32, 0, s>>>(B, P);
   const int g = c.force_blocks;
-#define LF(PR, MO) k_force<PR, MO><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
+  const bool ty = P.n_types > 1;
+#define LF(PR, MO, SP, TY) k_force<PR, MO, SP, TY><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
   if (P.precision == 0) {
     switch (mode) {
-      case FM_STEP: LF(0, FM_STEP); break;
-      case FM_FORCES: LF(0, FM_FORCES); break;
-      case FM_COUNT_NBR: LF(0, FM_COUNT_NBR); break;
-      default: LF(0, FM_LIST_NBR); break;
+      case FM_STEP: if (ty) LF(0, FM_STEP, false, true); else LF(0, FM_STEP, false, false); break;
+      case FM_FORCES: if (ty) LF(0, FM_FORCES, false, true); else LF(0, FM_FORCES, false, false); break;
+      case FM_COUNT_NBR: LF(0, FM_COUNT_NBR, false, false); break;
+      default: LF(0, FM_LIST_NBR, false, false); break;
     }
   } else {
     switch (mode) {
       case FM_STEP:
-        if (!P.walk && !P.grow && !P.die) k_force<1, FM_STEP, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, P);
-        else LF(1, FM_STEP);
+        if (ty) LF(1, FM_STEP, false, true);
+        else if (!P.walk && !P.grow && !P.die) LF(1, FM_STEP, true, false);
+        else LF(1, FM_STEP, false, false);
         break;
-      case FM_FORCES: LF(1, FM_FORCES); break;
-      case FM_COUNT_NBR: LF(1, FM_COUNT_NBR); break;
-      default: LF(1, FM_LIST_NBR); break;
+      case FM_FORCES: if (ty) LF(1, FM_FORCES, false, true); else LF(1, FM_FORCES, false, false); break;
+      case FM_COUNT_NBR: LF(1, FM_COUNT_NBR, false, false); break;
+      default: LF(1, FM_LIST_NBR, false, false); break;
     }
   }
 #undef LF

@@ -11,6 +11,9 @@
 //                 dirty-box marking for the static contract (Sec. 5)
 //   k_scan_*      exclusive scan of per-brick counts and occupancy
 //   k_scatter     agents into their brick's bucket (arrival order)
+//   k_brick_rank  rank of every brick among the in-domain bricks of its
+//                 simulation along the Morton curve (Sec. 4.2's order) or,
+//                 with curve = 1, along the Hilbert curve Sec. 4.2 compares
 //   k_brick_sort  per occupied brick, on chip: order by (box, storage index),
 //                 box ranges, and the compact per-agent records the force
 //                 kernel streams (box-local FP32 coordinates and radius)
@@ -106,6 +109,59 @@ __device__ long long morton_rank3(int x, int y, int z, int n0, int n1, int n2, i
       }
       sz[a] = half;
     }
+  }
+  return rank;
+}
+
+// Number of in-domain cells (x < n0, y < n1, z < n2) that come before (x, y,
+// z) on the 3D Hilbert curve of the 2^levels cube (the curve of Skilling's
+// transpose method: at each level the sub-cubes are visited in the Gray-code
+// order of their transformed bits, and the curve reflects or exchanges axes
+// on the lower levels according to the sub-cube it is in).  Going down the
+// levels, the state is the transform of the current node (which original axis
+// each transformed axis reads, and whether it is reflected) and the parity of
+// the final flip; at each level the in-domain cells of the sibling octants
+// whose digit is smaller than the target's are added.
+__device__ long long hilbert_rank3(int x, int y, int z, int n0, int n1, int n2, int levels) {
+  const int v[3] = {x, y, z}, n[3] = {n0, n1, n2};
+  int lo[3] = {0, 0, 0}, perm[3] = {0, 1, 2}, flip[3] = {0, 0, 0};
+  int tpar = 0;
+  long long rank = 0;
+  for (int q = levels - 1; q >= 0; --q) {
+    const int half = 1 << q;
+    const int b[3] = {(v[0] >> q) & 1, (v[1] >> q) & 1, (v[2] >> q) & 1};
+    // digit of a child with original bits c: transform, Gray-encode, flip
+    auto digit = [&](const int c[3]) {
+      const int X0 = c[perm[0]] ^ flip[0], X1 = c[perm[1]] ^ flip[1], X2 = c[perm[2]] ^ flip[2];
+      const int g0 = X0, g1 = X0 ^ X1, g2 = g1 ^ X2;
+      return ((g0 ^ tpar) << 2) | ((g1 ^ tpar) << 1) | (g2 ^ tpar);
+    };
+    const int dt = digit(b);
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c[3] = {cc & 1, (cc >> 1) & 1, (cc >> 2) & 1};
+      if (digit(c) >= dt) continue;
+      long long cnt = 1;
+      for (int d = 0; d < 3; ++d) {
+        const int a0 = lo[d] + c[d] * half;
+        const int a1 = min(a0 + half, n[d]);
+        cnt *= (a1 > a0) ? (long long)(a1 - a0) : 0ll;
+      }
+      rank += cnt;
+    }
+    // the curve's transform for the lower levels (the target's sub-cube)
+    const int X[3] = {b[perm[0]] ^ flip[0], b[perm[1]] ^ flip[1], b[perm[2]] ^ flip[2]};
+    const int gpar = X[0] ^ X[1] ^ X[2];
+    for (int i = 0; i < 3; ++i) {
+      if (X[i]) {
+        flip[0] ^= 1;
+      } else {
+        const int tp = perm[0], tf = flip[0];
+        perm[0] = perm[i]; flip[0] = flip[i];
+        perm[i] = tp; flip[i] = tf;
+      }
+    }
+    tpar ^= gpar;
+    for (int d = 0; d < 3; ++d) lo[d] += b[d] * half;
   }
   return rank;
 }
@@ -221,7 +277,9 @@ __global__ void k_brick_rank(DevBufs B, DevParams P) {
     const long long t = local / G.nr[0];
     const int iy = (int)(t % G.nr[1]);
     const int iz = (int)(t / G.nr[1]);
-    B.brick_table[g] = (int32_t)(base + morton_rank3(ix, iy, iz, G.nr[0], G.nr[1], G.nr[2], G.levels));
+    const long long r = (P.curve == 1) ? hilbert_rank3(ix, iy, iz, G.nr[0], G.nr[1], G.nr[2], G.levels)
+                                       : morton_rank3(ix, iy, iz, G.nr[0], G.nr[1], G.nr[2], G.levels);
+    B.brick_table[g] = (int32_t)(base + r);
     B.brick_count[g] = 0;
     B.dirty[g] = 0ull;
   }

@@ -37,6 +37,7 @@ DevParams make_dev_params(const bdm_params &P) {
   d.walk = P.walk_step > 0.0 ? 1 : 0;
   d.death_prob = P.death_prob;
   d.n_types = P.n_types > 1 ? P.n_types : 0;
+  d.curve = P.curve;
   for (int e = 0; e < 16; ++e) {
     d.type_k[e] = d.n_types ? P.type_k[e] : P.k;
     d.type_gamma[e] = d.n_types ? P.type_gamma[e] : P.gamma;
@@ -85,10 +86,9 @@ DevParams make_dev_params(const bdm_params &P) {
                         pow2i(-24) * (Rm + 2.0 * (double)d.graze));
     // the difference vector's error is at most sqrt(3) Ec, so the unit
     // direction of a pair at distance d is off by at most sqrt(3) Ec / d
-    d.dir_e = (float)(std::sqrt(3.0) * Ec);
-    // the fix-up pass evaluates pairs closer than 1 um in FP64: there the
-    // direction error dir_e / d of a pair exceeds 5e-6 of its force
-    d.close2 = 1.0f;
+    // (5e-6 / d at R = L = 11 um): pairs closer than 0.5 um, where that
+    // reaches 1e-5 of the pair's force, are evaluated in FP64
+    d.close2 = 0.25f;
     // grazing contacts shallower than 2e-3 um go to FP64 in place: above it
     // the bound gamma sqrt(rbar) graze_e / (2 sqrt(delta)) of one contact
     // stays near 2e-4, a small part of a dense agent's tolerance

@@ -9,7 +9,7 @@ from paper_2301_06984_gb300 import bdm
 from paper_2301_06984_gb300 import workloads as W
 
 ORACLE_KEYS = ("R", "L", "dt", "dmax", "k", "gamma", "adherence", "detect_static", "sort_every", "growth",
-               "divide_volume", "ratio_lo", "ratio_hi", "walk_step", "seed", "death_prob", "type_k", "type_gamma")
+               "divide_volume", "ratio_lo", "ratio_hi", "walk_step", "seed", "death_prob", "type_k", "type_gamma", "curve")
 
 
 def oracle_params(w, **over):
