@@ -310,8 +310,11 @@ class Simulation:
         return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
 
     def set_force_kernel(self, lanes=4):
-        """FP32 form: lanes per agent of the force kernel (1, 2, 4 = default,
-        8, 16, 32; -1 = chosen per box by its cost model)."""
+        """FP32 form: 1, 2, 4 (the default), 8, 16, 32 = the lane-per-agent
+        kernel with that many lanes per agent; -1 = the same with the lanes
+        chosen per box by its cost model; 0 = the tiled kernel; -3 = the sparse
+        kernel (the last two evaluate the contacts the FP32 error analysis does
+        not cover in double-float in place, with no fix-up pass)."""
         self._check(lib().bdm_set_force_kernel(self._h, int(lanes)))
 
     # ------------------------------------------------------------------ profiling

@@ -133,6 +133,7 @@ struct DevParams {
   float close2;                     // FP32 form: pairs closer than this (um^2) are evaluated
                                     // in FP64 (their FP32 direction is too rough)
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
+  int32_t df_shift;                 // fixed-point bits of contact_df's differences (|D| 2^s < 2^46)
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk, die;
   int32_t n_types;                  // > 1: the pair's constants are type_k / type_gamma[4 a + b]
@@ -321,9 +322,14 @@ struct LaunchCfg {
   int force_blocks;    // k_force
 };
 
-// default FP32 force kernel: the lane-per-agent kernel with 4 lanes per agent
-// (fastest of the choices on the dense and the static-core workloads)
+// FP32 force kernel choice (DevParams::lanes_fixed): FORCE_TILE selects the
+// tiled kernel (k_force_tile), FORCE_SPARSE the sparse kernel
+// (k_force_sparse), a positive value the lane-per-agent kernel with that many
+// lanes per agent, -1 the lane-per-agent kernel with the lanes chosen per box.
+// The default: 4 lanes per agent (fastest on dense tissue)
 #define FORCE_LANES_DEFAULT 4
+#define FORCE_TILE 0
+#define FORCE_SPARSE (-3)
 
 // brick weight classes of the force kernels' largest-first order (agents)
 #define FORCE_HEAVY_HI 1024

@@ -480,6 +480,102 @@ __device__ __forceinline__ float contact_int(const dbl4 &pq, const dbl4 &pc, int
   return fabsf(F);
 }
 
+// ---------------------------------------------------------------- double-float contact
+// Unevaluated sums h + l of two FP32 numbers (about 44 significant bits),
+// formed with error-free transformations: Knuth's TwoSum, the fast two-sum
+// for |a| >= |b|, and the product's exact error from one fused multiply-add
+// (Dekker 1971; the double-float arithmetic of Hida, Li and Bailey).  Every
+// operation is an explicitly rounded intrinsic, so no contraction changes them.
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_fast(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  const DF s = df_two_sum(x.h, y.h);
+  return df_fast(s.h, __fadd_rn(s.l, __fadd_rn(x.l, y.l)));
+}
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.h, y.h);
+  const float e = fmaf(x.h, y.l, fmaf(x.l, y.h, fmaf(x.h, y.h, -p)));
+  return df_fast(p, e);
+}
+// x / y and sqrt(x): an FP32 first approximation (the approximate reciprocal
+// and reciprocal square root suffice) corrected once by the exactly formed
+// residual
+__device__ __forceinline__ DF df_div(DF x, DF y) {
+  const float ry = __fdividef(1.0f, y.h);
+  const float q1 = __fmul_rn(x.h, ry);
+  const DF p = df_mul({q1, 0.f}, y);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p.h), p.l), x.l);  // x - q1 y
+  return df_fast(q1, __fmul_rn(r, ry));
+}
+__device__ __forceinline__ DF df_sqrt(DF x) {  // x > 0
+  const float rs = rsqrtf(x.h);
+  const float s = __fmul_rn(x.h, rs);
+  const DF p = df_two_prod(s, s);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(x.h, p.h), p.l), x.l);  // x - s^2
+  return df_fast(s, __fmul_rn(r, __fmul_rn(0.5f, rs)));
+}
+// an integer v, |v| < 2^46, times 2^-sh, as a double-float (exact)
+__device__ __forceinline__ DF df_of_fixed(long long v, int sh) {
+  const int hi = (int)(v >> 22);         // floor(v / 2^22), |hi| < 2^24
+  const int lo = (int)(v & 0x3FFFFFll);  // v - hi 2^22, in [0, 2^22)
+  const float sc = __int_as_float((127 - sh) << 23);
+  const DF r = df_fast(__fmul_rn((float)hi, 4194304.0f), (float)lo);
+  return {__fmul_rn(r.h, sc), __fmul_rn(r.l, sc)};
+}
+__device__ __forceinline__ int exp_of(double v) {  // |v| < 2^exp_of(v)
+  return (int)((__double_as_longlong(v) >> 52) & 0x7FF) - 1022;
+}
+
+// Force of a certain contact in double-float arithmetic, for the contacts
+// whose FP32 and exact-integer forms are too coarse: a force magnitude near
+// the sign change of k delta - gamma sqrt(rbar delta), where an absolute error
+// of eps delta in delta becomes about k/2 eps delta in F.  The positions'
+// differences are taken in fixed point 2^-sh (sh = 40, fewer bits where the
+// coordinates or the cutoff R need them: the truncation is below 2^-sh um per
+// coordinate), d, delta, rbar, sqrt(rbar delta) and F in double-float, the
+// direction (p_i - p_j) / d in FP32.  k and gamma: double-float pair constants.
+// Returns |F| and the force vector on the agent at pq.
+__device__ __forceinline__ float contact_df(const DevParams &P, const dbl4 &pq, const dbl4 &pc, DF k, DF gamma,
+                                            float &fx, float &fy, float &fz) {
+  int e = max(max(exp_of(pq.x), exp_of(pq.y)), max(exp_of(pq.z), exp_of(pc.x)));
+  e = max(e, max(exp_of(pc.y), exp_of(pc.z)));
+  const int sh = max(0, min(P.df_shift, 61 - e));
+  const DF Dx = df_of_fixed(to_fixed(pq.x, sh) - to_fixed(pc.x, sh), sh);
+  const DF Dy = df_of_fixed(to_fixed(pq.y, sh) - to_fixed(pc.y, sh), sh);
+  const DF Dz = df_of_fixed(to_fixed(pq.z, sh) - to_fixed(pc.z, sh), sh);
+  fx = fy = fz = 0.f;
+  const DF d2 = df_add(df_add(df_mul(Dx, Dx), df_mul(Dy, Dy)), df_mul(Dz, Dz));
+  if (!(d2.h > 0.f)) return 0.f;
+  const DF d = df_sqrt(d2);
+  const float rq = (float)pq.w, rc = (float)pc.w;  // exact: the radii are floats
+  const DF S = df_two_sum(rq, rc);
+  const DF delta = df_add(S, {-d.h, -d.l});
+  if (!(delta.h > 0.f)) return 0.f;
+  const DF rbar = df_div(df_two_prod(rq, rc), S);
+  const DF sq = df_sqrt(df_mul(rbar, delta));
+  const DF gs = df_mul(gamma, sq);
+  const DF F = df_add(df_mul(k, delta), {-gs.h, -gs.l});
+  const float Ff = __fadd_rn(F.h, F.l);
+  const float sc = __fdividef(Ff, d.h);
+  fx = __fmul_rn(sc, Dx.h);
+  fy = __fmul_rn(sc, Dy.h);
+  fz = __fmul_rn(sc, Dz.h);
+  return fabsf(Ff);
+}
+
 // The same, out of line (for the force kernel's rare use, so that its main
 // loop keeps its registers).
 __device__ __noinline__ float contact_int_call(const dbl4 &pq, const dbl4 &pc, int fs, float k, float gamma, float &fx,
@@ -1003,6 +1099,632 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   }
 }
 
+// ---------------------------------------------------------------- tiled FP32 force kernel
+// FP32 form, FM_STEP and FM_FORCES (lanes = 0).  A warp takes a box and its
+// agents in groups of up to 32 (lane a owns agent a of the group), stages the
+// box's 27-box stencil in chunks of TCH candidate records (neighbour-box
+// offset applied, as k_force stages them) and, per chunk:
+//  1. tests every computing agent of the group against the chunk, lane t
+//     holding candidates t and t + 32 in registers: the FP32 prefilter
+//     d^2 < R2_hi of k_force, bit for bit.  One ballot per candidate slot
+//     appends the passing (agent, candidate) pairs to the warp's pair list,
+//     agent after agent, so that each agent's pairs are contiguous and in
+//     candidate order;
+//  2. evaluates the list 32 pairs per warp instruction with k_force's
+//     decisions (FP32 outside the error bands, FP64 inside them) and its FP32
+//     arithmetic, each lane writing its pair's force over the list entry;
+//     the contacts whose FP32 force is not within the tolerance on their own
+//     (|F| below low_scale, near the sign change of k delta - gamma
+//     sqrt(rbar delta); grazing, delta < graze; close, d^2 < close2) go to a
+//     second list that is evaluated in double-float arithmetic (contact_df),
+//     again 32 pairs per warp instruction;
+//  3. has each owner lane add its agent's segment of the list in list order
+//     (summed per segment, then into the agent's total).
+// Every test slot and every evaluation slot is a lane of work whatever the
+// box's agent count.  Every contact's force is within the FP32 form's
+// tolerance where it is formed, so no agent needs the fix-up pass.  The sums
+// are deterministic (the same bits on every run), in a different order from
+// k_force's.
+#define TILE_WARPS 8
+#define TCH 64    // candidates per staged chunk (2 per lane)
+#define TPL 192   // entries of a warp's pair list (>= TCH: one agent's worst case)
+template <int MODE, bool TYPES>
+__global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, DevParams P) {
+  static_assert(MODE == FM_STEP || MODE == FM_FORCES, "the tiled kernel computes forces");
+  __shared__ int s_nocc[27];
+  __shared__ unsigned long long s_ndirty[27];
+  __shared__ int s_next;
+  __shared__ unsigned s_bcnt[64];
+  __shared__ uint8_t s_order[64];
+  __shared__ unsigned long long s_need;
+  __shared__ long long s_o;
+  __shared__ unsigned s_ctr[TILE_WARPS][4];  // candidates, neighbours, contacts, exact pairs
+  __shared__ float4 s_off[27];
+  __shared__ unsigned long long s_bb[TILE_WARPS][6];
+  __shared__ unsigned s_pre[TILE_WARPS][28], s_st[TILE_WARPS][28];
+  __shared__ float4 s_own[TILE_WARPS][32];          // the group's agents' FP32 records
+  __shared__ uint8_t s_otp[TILE_WARPS][32];         // TYPES: their types
+  __shared__ float4 s_c[TILE_WARPS][TCH];           // the staged chunk (offset applied)
+  __shared__ uint32_t s_kj[TILE_WARPS][TCH];        // its sorted positions
+  __shared__ uint8_t s_tp[TILE_WARPS][TCH];         // TYPES: its types
+  __shared__ float4 s_rec[TILE_WARPS][TPL];         // the pair list: entry, then result
+  __shared__ uint16_t s_dfl[TILE_WARPS][TPL];       // its contacts for the double-float pass
+  __shared__ float s_tkf[16], s_tgf[16];
+  __shared__ double s_tkd[16], s_tgd[16];
+  __shared__ DF s_tk2[16], s_tg2[16];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
+  const long long n_occ = C->n_occ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const long long step = C->step;
+  unsigned c_static = 0, c_moved = 0;
+  int wsim = -1;
+  int fetch_phase = 0;
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
+  }
+  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
+  if (lane < 4) s_ctr[warp][lane] = 0u;
+  if (threadIdx.x < 16) {  // one type: every entry holds k and gamma
+    s_tkd[threadIdx.x] = P.type_k[threadIdx.x];
+    s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
+    s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
+    s_tgf[threadIdx.x] = (float)P.type_gamma[threadIdx.x];
+    const float kh = (float)P.type_k[threadIdx.x], gh = (float)P.type_gamma[threadIdx.x];
+    s_tk2[threadIdx.x] = {kh, (float)(P.type_k[threadIdx.x] - (double)kh)};
+    s_tg2[threadIdx.x] = {gh, (float)(P.type_gamma[threadIdx.x] - (double)gh)};
+  }
+  // a staged slot past the chunk's end: a record no agent is near
+  const float4 far = make_float4(3.0e38f, 3.0e38f, 3.0e38f, 0.f);
+
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+      s_next = 0;
+    }
+    __syncthreads();
+    const long long o = s_o;
+    if (o < 0) break;
+    if (!BDM_IN(B.ctr, o < n_occ)) break;  // block-uniform
+    const int4 info = B.occ_info[o];
+    const SimGeom &G = B.geom[info.w];
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x;
+      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
+      int occ = -1;
+      unsigned long long dm = 0ull;
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
+        occ = B.brick_occ[rank];
+        if (use_static) dm = B.dirty[rank];
+      }
+      s_nocc[t] = occ;
+      s_ndirty[t] = dm;
+    }
+    if (threadIdx.x >= 64 && threadIdx.x < 128) s_bcnt[threadIdx.x - 64] = B.box_cnt[o * 64 + threadIdx.x - 64];
+    if (threadIdx.x == 32) s_need = use_static ? B.need[o] : ~0ull;
+    __syncthreads();
+    if (MODE == FM_STEP && info.w != wsim) {
+      flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+      wsim = info.w;
+    }
+    const double dt = G.dt;
+    const float dt_f = G.dt_f;
+    // boxes heaviest first (ties by box index)
+    if (threadIdx.x < 64) {
+      const unsigned c = s_bcnt[threadIdx.x];
+      unsigned r = 0;
+      for (int q = 0; q < 64; ++q) {
+        const unsigned cq = s_bcnt[q];
+        r += (cq > c) || (cq == c && q < (int)threadIdx.x);
+      }
+      s_order[r] = (uint8_t)threadIdx.x;
+    }
+    __syncthreads();
+
+    while (true) {
+      int kb = 0;
+      if (lane == 0) kb = atomicAdd(&s_next, 1);
+      kb = __shfl_sync(0xffffffffu, kb, 0);
+      if (kb >= 64) break;
+      const int lb = s_order[kb];
+      if (!((s_need >> lb) & 1ull)) continue;  // nothing left after the static pass
+      const unsigned qbase = B.box_start[o * 64 + lb], nq = B.box_cnt[o * 64 + lb];
+      if (nq == 0) continue;
+      int lx, ly, lz;
+      local_decode(lb, lx, ly, lz);
+      unsigned nb_st = 0, nb_cnt = 0;
+      bool nb_dirty = false;
+      if (lane < 27) {
+        const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
+        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+        const int lc = local_code(ax & 3, ay & 3, az & 3);
+        const int occ = s_nocc[bo];
+        if (occ >= 0) {
+          nb_st = B.box_start[(long long)occ * 64 + lc];
+          nb_cnt = B.box_cnt[(long long)occ * 64 + lc];
+        }
+        nb_dirty = (s_ndirty[bo] >> lc) & 1ull;
+      }
+      const bool clean = !__any_sync(0xffffffffu, nb_dirty);
+      unsigned pre = nb_cnt;
+      for (int of = 1; of < 32; of <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
+        if (lane >= of) pre += y;
+      }
+      const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
+      if (lane <= 27) s_pre[warp][lane] = pre - nb_cnt;  // s_pre[27] = ctot
+      if (lane < 27) s_st[warp][lane] = nb_st;
+      __syncwarp();
+      for (unsigned q0 = 0; q0 < nq; q0 += 32) {
+        const unsigned qi = q0 + (unsigned)lane;
+        bool valid = qi < nq;
+        unsigned kq = qbase + (valid ? qi : 0u);
+        if (!BDM_IN(B.ctr, (long long)kq < C->n)) { kq = 0; valid = false; }
+        uint32_t iq = B.perm[kq];
+        if (!BDM_IN(B.ctr, (long long)iq < B.cap)) { iq = 0; valid = false; }
+        const float4 cq = B.c32[kq];
+        const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
+        const bool is_static = use_static && clean && valid && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+        const bool compute = valid && !is_static;
+        const unsigned cmask = __ballot_sync(0xffffffffu, compute);
+        __syncwarp();  // the previous group's readers of s_own are done
+        s_own[warp][lane] = cq;
+        if (TYPES) s_otp[warp][lane] = B.tp[kq];
+        if (lane == 0) s_ctr[warp][0] += ctot * (unsigned)__popc(cmask);
+        float ffx = 0.f, ffy = 0.f, ffz = 0.f;  // this lane's agent's force
+        unsigned ncont = 0, nnb = 0;
+        unsigned my_lo = 0, my_hi = 0;  // this lane's agent's segment of the list
+        __syncwarp();
+        for (unsigned c0 = 0; cmask != 0u && c0 < ctot; c0 += TCH) {
+          // ---- stage the chunk: each lane locates its two positions in the
+          // stencil (binary search over the box prefix sums), loads them, and
+          // keeps them in registers for the test
+          float4 cr[2];
+          {
+            unsigned kjs[2];
+            int boxs[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+              const unsigned p = c0 + (unsigned)lane + 32u * m;
+              int lo = 0;
+#pragma unroll
+              for (int st = 16; st > 0; st >>= 1)
+                if (lo + st <= 26 && s_pre[warp][lo + st] <= p) lo += st;
+              boxs[m] = lo;
+              kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
+              if (!BDM_IN(B.ctr, p >= ctot || (long long)kjs[m] < C->n)) kjs[m] = 0;
+            }
+            float4 cs[2];
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+              if (c0 + (unsigned)lane + 32u * m < ctot) cs[m] = __ldg(&B.c32[kjs[m]]);
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {
+              const unsigned t = (unsigned)lane + 32u * m;
+              cr[m] = far;
+              if (c0 + t < ctot) {
+                const float4 of = s_off[boxs[m]];
+                cr[m] = make_float4(cs[m].x + of.x, cs[m].y + of.y, cs[m].z + of.z, cs[m].w);
+                s_c[warp][t] = cr[m];
+                s_kj[warp][t] = kjs[m];
+                if (TYPES) s_tp[warp][t] = B.tp[kjs[m]];
+              }
+            }
+          }
+          unsigned am = cmask;  // agents still to test against this chunk
+          while (true) {
+            // ---- test agents until the list could overflow
+            unsigned base = 0;
+            while (am != 0u && base + TCH <= TPL) {
+              const int a = __ffs(am) - 1;
+              am &= am - 1u;
+              const float4 qa = s_own[warp][a];
+              const bool p0 = dist2_f32(qa, cr[0]) < P.R2_hi_f;
+              const bool p1 = dist2_f32(qa, cr[1]) < P.R2_hi_f;
+              const unsigned b0 = __ballot_sync(0xffffffffu, p0), b1 = __ballot_sync(0xffffffffu, p1);
+              const unsigned n0 = __popc(b0);
+              const unsigned tag = ((unsigned)a << 8) | (unsigned)lane;
+              if (p0) reinterpret_cast<unsigned &>(s_rec[warp][base + __popc(b0 & lt)].x) = tag;
+              if (p1) reinterpret_cast<unsigned &>(s_rec[warp][base + n0 + __popc(b1 & lt)].x) = tag + 32u;
+              if (lane == a) my_lo = base;
+              base += n0 + __popc(b1);
+              if (lane == a) my_hi = base;
+            }
+            __syncwarp();
+            // ---- evaluate the list, 32 pairs per warp instruction
+            unsigned ndf = 0;  // contacts listed for the double-float pass
+            for (unsigned p0 = 0; p0 < base; p0 += 32u) {
+              const unsigned e = p0 + (unsigned)lane;
+              int r = 0;  // 0: no neighbour, 1: neighbour without force, 2: contact
+              bool risky = false;
+              if (e < base) {
+                const unsigned ent = reinterpret_cast<const unsigned &>(s_rec[warp][e].x);
+                const int a = (int)(ent >> 8);
+                const unsigned t = ent & 255u;
+                const unsigned kqa = qbase + q0 + (unsigned)a;
+                const unsigned kj = s_kj[warp][t];
+                float4 res = make_float4(0.f, 0.f, 0.f, 0.f);  // force on agent a
+                if (kj != kqa) {
+                  const float4 qa = s_own[warp][a];
+                  const float4 c = s_c[warp][t];
+                  const float ex = __fsub_rn(qa.x, c.x), ey = __fsub_rn(qa.y, c.y), ez = __fsub_rn(qa.z, c.z);
+                  const float d2 = fmaf(ex, ex, fmaf(ey, ey, __fmul_rn(ez, ez)));
+                  const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+                  const float s = __fadd_rn(qa.w, c.w), s2 = s * s;
+                  const float W = fmaf(s, P.cband1, s2 * P.cband2);
+                  const int ab = TYPES ? 4 * (int)s_otp[warp][a] + (int)s_tp[warp][t] : 0;
+                  const float kf = TYPES ? s_tkf[ab] : P.kf, gf = TYPES ? s_tgf[ab] : P.gammaf;
+                  const bool exact = band || (d2 > s2 - W && d2 < s2 + W);  // cutoff or contact in FP64
+                  if (!exact && d2 >= s2 + W) {
+                    r = 1;  // a neighbour, certainly no contact
+                  } else if (!exact) {
+                    r = 2;
+                    const ContactF32 k = contact_f32(d2, s, __fmul_rn(qa.w, c.w), kf, gf);
+                    // a contact whose FP32 force is not within the tolerance on
+                    // its own: near the sign change of F (|F| < low_scale),
+                    // grazing (delta < graze: sqrt(rbar delta) is steep in
+                    // delta) or close (d^2 < close2: the direction); it keeps
+                    // its list entry for the double-float pass
+                    risky = fabsf(k.fm) < P.low_scale || k.delta < P.graze || d2 < P.close2;
+                    res = make_float4(__fmul_rn(k.scf, ex), __fmul_rn(k.scf, ey), __fmul_rn(k.scf, ez), 0.f);
+                  } else {
+                    atomicAdd(&s_ctr[warp][3], 1u);
+                    double gx = 0.0, gy = 0.0, gz = 0.0;
+                    r = pair_f64_k(P.R2, TYPES ? s_tkd[ab] : P.k, TYPES ? s_tgd[ab] : P.gamma,
+                                   exact_of<1>(B, A, cur, kqa), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                    if (r == 2) res = make_float4((float)gx, (float)gy, (float)gz, 0.f);
+                  }
+                }
+                if (!risky) s_rec[warp][e] = res;
+              }
+              {
+                const unsigned bd = __ballot_sync(0xffffffffu, risky);
+                if (risky) s_dfl[warp][ndf + __popc(bd & lt)] = (uint16_t)e;
+                ndf += __popc(bd);
+              }
+              // this window's neighbours and contacts of each owner's agent
+              const unsigned bn = __ballot_sync(0xffffffffu, r > 0), bc = __ballot_sync(0xffffffffu, r == 2);
+              if (my_hi > p0 && my_lo < p0 + 32u) {
+                const unsigned lo = (my_lo > p0 ? my_lo : p0) - p0, hi = (my_hi < p0 + 32u ? my_hi : p0 + 32u) - p0;
+                const unsigned msk = ((hi == 32u) ? 0xffffffffu : ((1u << hi) - 1u)) & ~((1u << lo) - 1u);
+                nnb += __popc(bn & msk);
+                ncont += __popc(bc & msk);
+              }
+            }
+            __syncwarp();
+            // ---- the listed contacts in double-float (contact_df), 32 per
+            // warp instruction; each result replaces its entry
+            for (unsigned d0 = 0; d0 < ndf; d0 += 32u) {
+              if (d0 + (unsigned)lane < ndf) {
+                const unsigned e = s_dfl[warp][d0 + lane];
+                const unsigned ent = reinterpret_cast<const unsigned &>(s_rec[warp][e].x);
+                const int a = (int)(ent >> 8);
+                const unsigned t = ent & 255u;
+                const int ab = TYPES ? 4 * (int)s_otp[warp][a] + (int)s_tp[warp][t] : 0;
+                float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+                contact_df(P, exact_of<1>(B, A, cur, qbase + q0 + (unsigned)a), exact_of<1>(B, A, cur, s_kj[warp][t]),
+                           s_tk2[ab], s_tg2[ab], res.x, res.y, res.z);
+                s_rec[warp][e] = res;
+              }
+            }
+            if (lane == 0 && ndf) s_ctr[warp][3] += ndf;
+            __syncwarp();
+            // ---- each owner sums its agent's segment in list order, then
+            // adds that sum to the agent's (a two-level sum: the rounding of
+            // a long sequential sum of large, cancelling pair forces is what
+            // a dense cluster would feel)
+            {
+              float sx = 0.f, sy = 0.f, sz = 0.f;
+              for (unsigned u = my_lo; u < my_hi; ++u) {
+                const float4 v = s_rec[warp][u];
+                sx += v.x;
+                sy += v.y;
+                sz += v.z;
+              }
+              ffx += sx;
+              ffy += sy;
+              ffz += sz;
+            }
+            my_lo = my_hi = 0;
+            __syncwarp();
+            if (am == 0u) break;
+          }
+        }
+        // ---- per agent: the epilogue
+        {
+          const unsigned gn = __reduce_add_sync(0xffffffffu, valid ? nnb : 0u);
+          const unsigned gc = __reduce_add_sync(0xffffffffu, valid ? ncont : 0u);
+          if (lane == 0) { s_ctr[warp][1] += gn; s_ctr[warp][2] += gc; }
+        }
+        if (!compute) continue;  // static agents: finished by the static pass
+        double px = 0.0, py = 0.0, pz = 0.0;
+        if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
+        finish_agent<1, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, false, ffx, ffy, ffz, 0.0, 0.0, 0.0, nnb,
+                              ncont, c_static, c_moved, s_bb[warp], px, py, pz);
+      }
+    }
+  }
+  if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+  __syncwarp();
+  const unsigned long long t_static = wsum64(c_static), t_moved = wsum64(c_moved), t_cand = s_ctr[warp][0],
+                           t_nbr = s_ctr[warp][1], t_cont = s_ctr[warp][2], t_exact = s_ctr[warp][3];
+  if (lane == 0) {
+    if (t_static) atomicAdd(&C->a_static, t_static);
+    if (t_moved) atomicAdd(&C->a_moved, t_moved);
+    if (t_cand) atomicAdd(&C->a_cand, t_cand);
+    if (t_nbr) atomicAdd(&C->a_nbr, t_nbr);
+    if (t_cont) atomicAdd(&C->a_contact, t_cont);
+    if (t_exact) atomicAdd(&C->a_exact, t_exact);
+  }
+}
+
+// ---------------------------------------------------------------- sparse FP32 force kernel
+// FP32 form, FM_STEP and FM_FORCES (lanes = -3), for sparse tissue: boxes of
+// one to a few agents (a shell around a static core, the small simulations of
+// an ensemble), where the per-box work of the box-per-warp kernels (stencil
+// set-up, staging, lists) is shared by too few agents.  One CTA per occupied
+// brick (heaviest first, the static pass's work list as in k_force); its
+// threads take the brick's agents one per lane, in rounds of the CTA size, and
+// each lane walks its own agent's 27-box stencil in the canonical order,
+// testing every candidate with k_force's FP32 prefilter and deciding
+// neighbour and contact exactly as k_force does (FP32 outside the error
+// bands, FP64 in place inside them).  A contact the FP32 error analysis covers
+// is added in place; the others (|F| < low_scale, delta < graze, d^2 < close2)
+// are queued per lane and evaluated by the warp in double-float (contact_df),
+// 32 pairs per warp instruction, after each round; the owner lane adds their
+// results in its queue order.  A lane whose queue is full evaluates the contact
+// itself.  No agent is listed for the fix-up pass.
+#define SP_WARPS 4
+#define SP_Q 8    // double-float contacts a lane queues per round
+template <int MODE, bool TYPES>
+__global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, DevParams P) {
+  static_assert(MODE == FM_STEP || MODE == FM_FORCES, "the sparse kernel computes forces");
+  __shared__ int s_nocc[27];
+  __shared__ unsigned long long s_ndirty[27];
+  __shared__ unsigned s_bst[65];                  // the brick's box starts and its end
+  __shared__ unsigned long long s_need, s_clean;  // boxes with work; boxes with a clean stencil
+  __shared__ long long s_o;
+  __shared__ float4 s_off[27];
+  __shared__ unsigned long long s_bb[SP_WARPS][6];
+  __shared__ uint32_t s_dq[SP_WARPS][SP_Q][32];   // each lane's queued candidates (sorted positions)
+  __shared__ float4 s_dr[SP_WARPS][SP_Q][32];     // and their double-float forces
+  __shared__ uint32_t s_dk[SP_WARPS][32];         // each lane's agent (sorted position)
+  __shared__ float s_tkf[16], s_tgf[16];
+  __shared__ double s_tkd[16], s_tgd[16];
+  __shared__ DF s_tk2[16], s_tg2[16];
+  DevCounters *C = B.ctr;
+  if (C->error) return;
+  const AgentSet A = *B.A;
+  const int cur = (int)(C->step & 1), nxt = cur ^ 1;
+  const bool use_static = (MODE == FM_STEP) && P.detect_static && C->history_valid;
+  const long long n_occ = C->n_occ;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long step = C->step;
+  unsigned c_static = 0, c_moved = 0;
+  int wsim = -1;
+  int fetch_phase = 0;
+  if (threadIdx.x < 27) {
+    const int t = threadIdx.x;
+    s_off[t] = make_float4((float)(t % 3 - 1) * P.Lf, (float)((t / 3) % 3 - 1) * P.Lf, (float)(t / 9 - 1) * P.Lf, 0.f);
+  }
+  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
+  if (threadIdx.x < 16) {  // one type: every entry holds k and gamma
+    s_tkd[threadIdx.x] = P.type_k[threadIdx.x];
+    s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
+    s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
+    s_tgf[threadIdx.x] = (float)P.type_gamma[threadIdx.x];
+    const float kh = (float)P.type_k[threadIdx.x], gh = (float)P.type_gamma[threadIdx.x];
+    s_tk2[threadIdx.x] = {kh, (float)(P.type_k[threadIdx.x] - (double)kh)};
+    s_tg2[threadIdx.x] = {gh, (float)(P.type_gamma[threadIdx.x] - (double)gh)};
+  }
+  unsigned n_cand = 0, n_nbr = 0, n_cont = 0, n_exact = 0;  // this thread's statistics
+
+  while (true) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+    __syncthreads();
+    const long long o = s_o;
+    if (o < 0) break;
+    if (!BDM_IN(B.ctr, o < n_occ)) break;  // block-uniform
+    const int4 info = B.occ_info[o];
+    const SimGeom &G = B.geom[info.w];
+    if (threadIdx.x < 27) {
+      const int t = threadIdx.x;
+      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
+      int occ = -1;
+      unsigned long long dm = 0ull;
+      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+        const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
+        occ = B.brick_occ[rank];
+        if (use_static) dm = B.dirty[rank];
+      }
+      s_nocc[t] = occ;
+      s_ndirty[t] = dm;
+    }
+    if (threadIdx.x >= 32 && threadIdx.x < 96) s_bst[threadIdx.x - 32] = B.box_start[o * 64 + threadIdx.x - 32];
+    if (threadIdx.x == 96) {
+      s_need = use_static ? B.need[o] : ~0ull;
+      s_bst[64] = B.box_start[o * 64 + 63] + B.box_cnt[o * 64 + 63];
+      s_clean = 0ull;
+    }
+    __syncthreads();
+    if (use_static && threadIdx.x < 64) {
+      // a box is clean when no box of its 27-box stencil is dirty
+      int lx, ly, lz;
+      local_decode((int)threadIdx.x, lx, ly, lz);
+      bool dirty = false;
+      for (int t = 0; t < 27; ++t) {
+        const int ax = lx + t % 3 - 1, ay = ly + (t / 3) % 3 - 1, az = lz + t / 9 - 1;
+        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+        dirty |= (s_ndirty[bo] >> local_code(ax & 3, ay & 3, az & 3)) & 1ull;
+      }
+      if (!dirty) atomicOr(&s_clean, 1ull << threadIdx.x);
+    }
+    __syncthreads();
+    if (MODE == FM_STEP && info.w != wsim) {
+      flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+      wsim = info.w;
+    }
+    const double dt = G.dt;
+    const float dt_f = G.dt_f;
+    const unsigned b0 = s_bst[0], nb = s_bst[64] - s_bst[0];
+    // rounds of one agent per thread (CTA-uniform trip count)
+    for (unsigned r0 = 0; r0 < nb; r0 += SP_WARPS * 32) {
+      const unsigned i = r0 + threadIdx.x;
+      bool valid = i < nb;
+      const unsigned kq = b0 + (valid ? i : 0u);
+      int lb = 0;  // the agent's box: the last box starting at or before kq
+#pragma unroll
+      for (int st = 32; st > 0; st >>= 1)
+        if (lb + st < 64 && s_bst[lb + st] <= kq) lb += st;
+      valid = valid && ((s_need >> lb) & 1ull);
+      if (!BDM_IN(B.ctr, !valid || (long long)kq < C->n)) valid = false;
+      uint32_t iq = valid ? B.perm[kq] : 0u;
+      if (!BDM_IN(B.ctr, (long long)iq < B.cap)) { iq = 0; valid = false; }
+      const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
+      const bool is_static = use_static && valid && ((s_clean >> lb) & 1ull) && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+      const bool compute = valid && !is_static;
+      const float4 cq = B.c32[kq];
+      const int tq4 = TYPES ? 4 * (int)B.tp[kq] : 0;
+      s_dk[warp][lane] = kq;
+      float ffx = 0.f, ffy = 0.f, ffz = 0.f;
+      unsigned nnb = 0, ncont = 0, nq = 0;
+      if (compute) {
+        int lx, ly, lz;
+        local_decode(lb, lx, ly, lz);
+        for (int sb = 0; sb < 27; ++sb) {
+          const int ax = lx + sb % 3 - 1, ay = ly + (sb / 3) % 3 - 1, az = lz + sb / 9 - 1;
+          const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                         ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+          const int occ = s_nocc[bo];
+          if (occ < 0) continue;
+          const long long bx = (long long)occ * 64 + local_code(ax & 3, ay & 3, az & 3);
+          const unsigned st = B.box_start[bx], cnt = B.box_cnt[bx];
+          n_cand += cnt;
+          const float4 of = s_off[sb];
+          for (unsigned j = 0; j < cnt; ++j) {
+            const unsigned kj = st + j;
+            if (!BDM_IN(B.ctr, (long long)kj < C->n)) break;
+            const float4 cs = __ldg(&B.c32[kj]);
+            const float4 c = make_float4(cs.x + of.x, cs.y + of.y, cs.z + of.z, cs.w);
+            const float d2 = dist2_f32(cq, c);
+            if (!(d2 < P.R2_hi_f) || kj == kq) continue;
+            const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+            const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
+            const float W = fmaf(s, P.cband1, s2 * P.cband2);
+            if (!band && d2 >= s2 + W) {  // a neighbour, certainly no contact
+              nnb++;
+              continue;
+            }
+            const int ab = tq4 + (TYPES ? (int)B.tp[kj] : 0);
+            if (band || d2 > s2 - W) {  // cutoff or contact undecided in FP32: FP64
+              n_exact++;
+              double gx = 0.0, gy = 0.0, gz = 0.0;
+              const int r = pair_f64_k(P.R2, TYPES ? s_tkd[ab] : P.k, TYPES ? s_tgd[ab] : P.gamma,
+                                       exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+              nnb += (r > 0);
+              ncont += (r == 2);
+              if (r == 2) { ffx += (float)gx; ffy += (float)gy; ffz += (float)gz; }
+              continue;
+            }
+            nnb++;
+            ncont++;
+            const float kf = TYPES ? s_tkf[ab] : P.kf, gf = TYPES ? s_tgf[ab] : P.gammaf;
+            const ContactF32 k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), kf, gf);
+            if (fabsf(k.fm) < P.low_scale || k.delta < P.graze || d2 < P.close2) {
+              // not covered by the FP32 error analysis: double-float, queued
+              // for the warp (or here when the queue is full)
+              n_exact++;
+              if (nq < SP_Q) {
+                s_dq[warp][nq][lane] = kj;
+                nq++;
+              } else {
+                float tx, ty, tz;
+                contact_df(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), s_tk2[ab], s_tg2[ab], tx, ty,
+                           tz);
+                ffx += tx; ffy += ty; ffz += tz;
+              }
+              continue;
+            }
+            ffx = fmaf(k.scf, __fsub_rn(cq.x, c.x), ffx);
+            ffy = fmaf(k.scf, __fsub_rn(cq.y, c.y), ffy);
+            ffz = fmaf(k.scf, __fsub_rn(cq.z, c.z), ffz);
+          }
+        }
+      }
+      // ---- the warp's queued contacts in double-float, 32 per warp
+      // instruction (lanes' queues pooled in lane order), then each owner
+      // adds its own in its queue order
+      {
+        unsigned inc = nq;
+        for (int of = 1; of < 32; of <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, inc, of);
+          if (lane >= of) inc += y;
+        }
+        const unsigned tot = __shfl_sync(0xffffffffu, inc, 31);
+        if (tot) {
+          __syncwarp();  // the lanes' queues and agents are written
+          const unsigned mine = inc - nq;
+          // pooled entry e belongs to the last lane whose first entry is <= e
+          // (a lane without entries starts where the next one does)
+          for (unsigned t0 = 0; t0 < tot; t0 += 32u) {
+            const unsigned e = t0 + (unsigned)lane;
+            int ow = 0;
+            for (int of = 16; of > 0; of >>= 1) {
+              const unsigned so = __shfl_sync(0xffffffffu, mine, ow + of);
+              if (so <= e) ow += of;
+            }
+            const unsigned sow = __shfl_sync(0xffffffffu, mine, ow);
+            if (e < tot) {
+              const unsigned sl = e - sow;
+              const unsigned kj = s_dq[warp][sl][ow], kqo = s_dk[warp][ow];
+              const int ab = TYPES ? 4 * (int)B.tp[kqo] + (int)B.tp[kj] : 0;
+              float4 rr = make_float4(0.f, 0.f, 0.f, 0.f);
+              contact_df(P, exact_of<1>(B, A, cur, kqo), exact_of<1>(B, A, cur, kj), s_tk2[ab], s_tg2[ab], rr.x, rr.y,
+                         rr.z);
+              s_dr[warp][sl][ow] = rr;
+            }
+          }
+          __syncwarp();
+          for (unsigned u = 0; u < nq; ++u) {
+            const float4 v = s_dr[warp][u][lane];
+            ffx += v.x;
+            ffy += v.y;
+            ffz += v.z;
+          }
+          __syncwarp();
+        }
+      }
+      if (valid) { n_nbr += nnb; n_cont += ncont; }
+      if (!compute) continue;  // static agents: finished by the static pass
+      double px = 0.0, py = 0.0, pz = 0.0;
+      if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
+      finish_agent<1, MODE>(B, P, A, cur, nxt, step, dt, dt_f, iq, fl, false, ffx, ffy, ffz, 0.0, 0.0, 0.0, nnb,
+                            ncont, c_static, c_moved, s_bb[warp], px, py, pz);
+    }
+  }
+  if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+  __syncwarp();
+  const unsigned long long t_moved = wsum64(c_moved), t_cand = wsum64(n_cand), t_nbr = wsum64(n_nbr),
+                           t_cont = wsum64(n_cont), t_exact = wsum64(n_exact);
+  if (lane == 0) {
+    if (t_moved) atomicAdd(&C->a_moved, t_moved);
+    if (t_cand) atomicAdd(&C->a_cand, t_cand);
+    if (t_nbr) atomicAdd(&C->a_nbr, t_nbr);
+    if (t_cont) atomicAdd(&C->a_contact, t_cont);
+    if (t_exact) atomicAdd(&C->a_exact, t_exact);
+  }
+}
+
 // ---------------------------------------------------------------- static pass
 // Static agents (FM_STEP with static detection, before the force kernel).  A
 // box is clean when no box of its 27-box stencil is dirty; an agent of a clean
@@ -1120,16 +1842,16 @@ __global__ void k_reset_work(DevBufs B) {
   B.ctr->fix_n = 0;
 }
 
-// ---------------------------------------------------------------- FP64 fix-up (FP32 form)
+// ---------------------------------------------------------------- fix-up pass (FP32 form)
 // The FP32-form agents that the force kernel listed (an FP32 error bound not
 // small against the agent's tolerance, or a summed pair-force magnitude so
 // small that the absolute floor dominates) are evaluated again here, one warp
 // per agent: the lanes walk the agent's 27-box stencil.  A pair the FP32
-// bands cannot decide (cutoff or contact) and a contact whose force magnitude
-// is below low_scale (near the sign change of k delta - gamma sqrt(rbar delta))
-// go to the warp's list of FP64 pairs; a grazing contact (delta < graze) and a
-// close pair (d^2 < close2) take the exact-integer geometry of contact_int; the
-// other
+// bands cannot decide (cutoff or contact) goes to the warp's list of FP64
+// pairs; a contact whose force magnitude is below low_scale (near the sign
+// change of k delta - gamma sqrt(rbar delta)) takes the double-float
+// arithmetic of contact_df; a grazing contact (delta < graze) and a close pair
+// (d^2 < close2) take the exact-integer geometry of contact_int; the other
 // contacts are summed exactly as the force kernel does.  The list is evaluated
 // in FP64 32 pairs per warp instruction (an FP64 instruction costs GB300's slow
 // FP64 pipe as much for one active lane as for 32) and summed in list order.
@@ -1145,6 +1867,7 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
   __shared__ unsigned long long s_bb[FIX_WARPS][6];
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
+  __shared__ DF s_tk2[16], s_tg2[16];
   __shared__ float4 s_fc[FIX_WARPS][FIX_BATCH][32];
   __shared__ unsigned s_fk[FIX_WARPS][FIX_BATCH][32];
   __shared__ uint8_t s_fb[FIX_WARPS][FIX_BATCH][32];
@@ -1158,6 +1881,9 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
     s_tgd[threadIdx.x] = P.type_gamma[threadIdx.x];
     s_tkf[threadIdx.x] = (float)P.type_k[threadIdx.x];
     s_tgf[threadIdx.x] = (float)P.type_gamma[threadIdx.x];
+    const float kh = (float)P.type_k[threadIdx.x], gh = (float)P.type_gamma[threadIdx.x];
+    s_tk2[threadIdx.x] = {kh, (float)(P.type_k[threadIdx.x] - (double)kh)};
+    s_tg2[threadIdx.x] = {gh, (float)(P.type_gamma[threadIdx.x] - (double)gh)};
   }
   __syncthreads();
   const AgentSet A = *B.A;
@@ -1281,22 +2007,29 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
                 risky = band || d2 > s2 - W;
                 if (!risky) {
                   // a certain contact: the force kernel's FP32 arithmetic, or
-                  // the exact-geometry path where that is too coarse; a force
-                  // magnitude below low_scale sits near the root of
-                  // k delta = gamma sqrt(rbar delta), where an FP32 delta's
-                  // rounding (k/2 * delta * eps) is not small against the
-                  // absolute floor: FP64 (list)
+                  // where that is too coarse: a force magnitude below
+                  // low_scale sits near the root of k delta = gamma
+                  // sqrt(rbar delta), where an FP32 delta's rounding (about
+                  // k/2 delta eps) is not small against the absolute floor
+                  // (double-float, contact_df); a grazing or close contact
+                  // needs the exact geometry (contact_int)
                   const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
                   const ContactF32 k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
-                  risky = fabsf(k.fm) < P.low_scale;
-                  if (!risky && (k.delta < P.graze || d2 < P.close2)) {
+                  if (fabsf(k.fm) < P.low_scale) {
+                    float tx, ty, tz;
+                    contact_df(P, dq, exact_of<1>(B, A, cur, kj), s_tk2[ab], s_tg2[ab], tx, ty, tz);
+                    hx += (double)tx;
+                    hy += (double)ty;
+                    hz += (double)tz;
+                    n_exact++;
+                  } else if (k.delta < P.graze || d2 < P.close2) {
                     float tx, ty, tz;
                     contact_int(dq, exact_of<1>(B, A, cur, kj), P.fix_shift, s_tkf[ab], s_tgf[ab], tx, ty, tz);
                     hx += (double)tx;
                     hy += (double)ty;
                     hz += (double)tz;
                     n_exact++;
-                  } else if (!risky) {
+                  } else {
                     gx = fmaf(k.scf, ex, gx);
                     gy = fmaf(k.scf, ey, gy);
                     gz = fmaf(k.scf, ez, gz);
@@ -1627,6 +2360,8 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
   const int g = c.force_blocks;
   const bool ty = P.n_types > 1;
 #define LF(PR, MO, SP, TY) k_force<PR, MO, SP, TY><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
+#define LT(MO, TY) k_force_tile<MO, TY><<<g, TILE_WARPS * 32, 0, s>>>(B, P)
+#define LS(MO, TY) k_force_sparse<MO, TY><<<2 * g, SP_WARPS * 32, 0, s>>>(B, P)
   if (P.precision == 0) {
     switch (mode) {
       case FM_STEP: if (ty) LF(0, FM_STEP, false, true); else LF(0, FM_STEP, false, false); break;
@@ -1637,29 +2372,45 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
   } else {
     switch (mode) {
       case FM_STEP:
-        if (ty) LF(1, FM_STEP, false, true);
+        if (P.lanes_fixed == FORCE_TILE) {
+          if (ty) LT(FM_STEP, true); else LT(FM_STEP, false);
+        } else if (P.lanes_fixed == FORCE_SPARSE) {
+          if (ty) LS(FM_STEP, true); else LS(FM_STEP, false);
+        } else if (ty) LF(1, FM_STEP, false, true);
         else if (!P.walk && !P.grow && !P.die) LF(1, FM_STEP, true, false);
         else LF(1, FM_STEP, false, false);
         break;
-      case FM_FORCES: if (ty) LF(1, FM_FORCES, false, true); else LF(1, FM_FORCES, false, false); break;
+      case FM_FORCES:
+        if (P.lanes_fixed == FORCE_TILE) {
+          if (ty) LT(FM_FORCES, true); else LT(FM_FORCES, false);
+        } else if (P.lanes_fixed == FORCE_SPARSE) {
+          if (ty) LS(FM_FORCES, true); else LS(FM_FORCES, false);
+        } else if (ty) LF(1, FM_FORCES, false, true);
+        else LF(1, FM_FORCES, false, false);
+        break;
       case FM_COUNT_NBR: LF(1, FM_COUNT_NBR, false, false); break;
       default: LF(1, FM_LIST_NBR, false, false); break;
     }
   }
 #undef LF
+#undef LT
+#undef LS
   if (mode == FM_FORCES) launch_force_fix(B, P, c, mode, s);
 }
 
 // the FP64 fix-up pass of the FP32 form, after launch_force (FM_STEP: its own
 // phase of an iteration; FM_FORCES: part of launch_force)
 void launch_force_fix(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
-  if (P.precision != 1) return;
+  // the tiled and sparse kernels list no agent
+  if (P.precision != 1 || P.lanes_fixed == FORCE_TILE || P.lanes_fixed == FORCE_SPARSE) return;
   if (mode == FM_STEP) k_force_fix<FM_STEP><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
   if (mode == FM_FORCES) k_force_fix<FM_FORCES><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
 }
 
 int force_launches(const DevParams &P) { (void)P; return 2; }
-int force_fix_launches(const DevParams &P) { return P.precision == 1 ? 1 : 0; }
+int force_fix_launches(const DevParams &P) {
+  return (P.precision == 1 && P.lanes_fixed != FORCE_TILE && P.lanes_fixed != FORCE_SPARSE) ? 1 : 0;
+}
 
 void launch_divide(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
   if (!P.grow && !P.die) return;

@@ -51,6 +51,12 @@ DevParams make_dev_params(const bdm_params &P) {
   if (sft > 40) sft = 40;
   if (sft < 0) sft = 0;
   d.fix_shift = sft;
+  // contact_df: a contact's coordinate differences (|D| < R) in fixed point
+  // 2^-s with |D| 2^s < 2^46 (two exact 24-bit halves), at most 2^-40 um
+  {
+    const int lr = (int)std::ceil(std::log2(std::max(d.R, 1.0) * 1.0000001));
+    d.df_shift = std::max(0, std::min(40, 46 - lr));
+  }
   double Lfix = std::round(d.L * pow2i(sft) / 128.0) * 128.0;
   d.L_fix = (long long)Lfix;
   d.Lf = (float)(Lfix * pow2i(-sft));

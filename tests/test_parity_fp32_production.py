@@ -25,25 +25,32 @@ def _cuda():
     yield
 
 
-def test_production_kernel_forces_blobs_100k_iterations_1_to_10():
-    # no walk, no growth: the per-axis epilogue instantiation that the 10M
-    # benchmark runs, 4 lanes per agent; iteration 1 is a sort step
+@pytest.mark.parametrize("lanes", [4, 0, -3])
+def test_production_kernel_forces_blobs_100k_iterations_1_to_10(lanes):
+    # no walk, no growth: the step instantiation that the 10M benchmark runs
+    # (the lane-per-agent kernel's per-axis epilogue, 4 lanes per agent, the
+    # default), the tiled kernel (lanes 0) and the sparse kernel (lanes -3);
+    # iteration 1 is a sort step
     w = H.small_blobs(n=100_000, seed=3)
     s = H.gpu_sim(w, precision="fp32", keep_forces=True)
+    s.set_force_kernel(lanes)
     P = H.oracle_params(w)
     for it in range(1, 11):
-        H.production_step_vs_oracle(s, P, what="blobs 100k iteration %d, production kernel" % it)
+        H.production_step_vs_oracle(s, P, what="blobs 100k iteration %d, kernel lanes=%d" % (it, lanes))
 
 
-def test_production_kernel_forces_core_shell_with_walk():
+@pytest.mark.parametrize("lanes", [4, 0, -3])
+def test_production_kernel_forces_core_shell_with_walk(lanes):
     # random walk on the shell and the static skip: the shared step
-    # instantiation with the one-lane epilogue, after the static pass
+    # instantiation with the one-lane epilogue, after the static pass, for
+    # the lane-per-agent, tiled and sparse kernels
     w = W.core_shell(n=20000, seed=5)
     s = H.gpu_sim(w, precision="fp32", keep_forces=True)
+    s.set_force_kernel(lanes)
     P = H.oracle_params(w)
     n_static = 0
     for it in range(1, 7):
-        H.production_step_vs_oracle(s, P, what="core+shell 20k iteration %d, walk kernel" % it)
+        H.production_step_vs_oracle(s, P, what="core+shell 20k iteration %d, kernel lanes=%d" % (it, lanes))
         n_static += int(s.last_static().sum())
     assert n_static > 0.5 * 5 * w.n
 
