@@ -1472,8 +1472,8 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
 // an ensemble), where the per-box work of the box-per-warp kernels (stencil
 // set-up, staging, lists) is shared by too few agents.  One CTA per occupied
 // brick (heaviest first, the static pass's work list as in k_force); its
-// threads take the brick's agents one per lane, in rounds of the CTA size, and
-// each lane walks its own agent's 27-box stencil in the canonical order,
+// threads take the agents of its boxes with work one per lane, in rounds of
+// the CTA size, and each lane walks its own agent's 27-box stencil in the canonical order,
 // testing every candidate with k_force's FP32 prefilter and deciding
 // neighbour and contact exactly as k_force does (FP32 outside the error
 // bands, FP64 in place inside them).  A contact the FP32 error analysis covers
@@ -1497,6 +1497,7 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
   __shared__ uint32_t s_dq[SP_WARPS][SP_Q][32];   // each lane's queued candidates (sorted positions)
   __shared__ float4 s_dr[SP_WARPS][SP_Q][32];     // and their double-float forces
   __shared__ uint32_t s_dk[SP_WARPS][32];         // each lane's agent (sorted position)
+  __shared__ unsigned s_ncum[65];                 // agents of boxes with work before each box
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
   __shared__ DF s_tk2[16], s_tg2[16];
@@ -1570,23 +1571,38 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
       if (!dirty) atomicOr(&s_clean, 1ull << threadIdx.x);
     }
     __syncthreads();
+    if (threadIdx.x < 32) {
+      // exclusive prefix of the agent counts of the boxes with work (two
+      // boxes per lane)
+      const int l2 = 2 * (int)threadIdx.x;
+      const unsigned a0 = ((s_need >> l2) & 1ull) ? s_bst[l2 + 1] - s_bst[l2] : 0u;
+      const unsigned a1 = ((s_need >> (l2 + 1)) & 1ull) ? s_bst[l2 + 2] - s_bst[l2 + 1] : 0u;
+      unsigned inc = a0 + a1;
+      for (int of = 1; of < 32; of <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, inc, of);
+        if ((int)threadIdx.x >= of) inc += y;
+      }
+      s_ncum[l2] = inc - a0 - a1;
+      s_ncum[l2 + 1] = inc - a1;
+      if (threadIdx.x == 31) s_ncum[64] = inc;
+    }
+    __syncthreads();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
     const double dt = G.dt;
     const float dt_f = G.dt_f;
-    const unsigned b0 = s_bst[0], nb = s_bst[64] - s_bst[0];
+    const unsigned nw = s_ncum[64];  // agents of the brick's boxes with work
     // rounds of one agent per thread (CTA-uniform trip count)
-    for (unsigned r0 = 0; r0 < nb; r0 += SP_WARPS * 32) {
+    for (unsigned r0 = 0; r0 < nw; r0 += SP_WARPS * 32) {
       const unsigned i = r0 + threadIdx.x;
-      bool valid = i < nb;
-      const unsigned kq = b0 + (valid ? i : 0u);
-      int lb = 0;  // the agent's box: the last box starting at or before kq
+      bool valid = i < nw;
+      int lb = 0;  // the agent's box: the last box with work whose first agent is at or before i
 #pragma unroll
       for (int st = 32; st > 0; st >>= 1)
-        if (lb + st < 64 && s_bst[lb + st] <= kq) lb += st;
-      valid = valid && ((s_need >> lb) & 1ull);
+        if (lb + st < 64 && s_ncum[lb + st] <= i) lb += st;
+      const unsigned kq = valid ? s_bst[lb] + (i - s_ncum[lb]) : s_bst[0];
       if (!BDM_IN(B.ctr, !valid || (long long)kq < C->n)) valid = false;
       uint32_t iq = valid ? B.perm[kq] : 0u;
       if (!BDM_IN(B.ctr, (long long)iq < B.cap)) { iq = 0; valid = false; }

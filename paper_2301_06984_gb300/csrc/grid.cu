@@ -488,10 +488,12 @@ __global__ void k_scatter(DevBufs B) {
 // --------------------------------------------------------------- brick sort
 #define BS_THREADS 256
 
-// Bricks of at most BSW_MAX agents (most bricks of sparse workloads) are
-// sorted by k_brick_sort_small, one warp per brick, with the same result;
-// k_brick_sort takes the rest, one block per brick.
-#define BSW_MAX 128
+// Bricks of at most BSW_MAX agents (most bricks of sparse workloads, and the
+// bricks of a tissue at one to four agents per box) are sorted by
+// k_brick_sort_small, one warp per brick, with the same result; k_brick_sort
+// takes the rest, one block per brick.
+#define BSW_MAX 320
+static_assert(BSW_MAX < FORCE_HEAVY_HI, "the warp-per-brick sort lists no brick at the heavy list front");
 #define BSW_WARPS 8
 #define BS_SMEM_M 4096
 
@@ -636,7 +638,7 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
   __shared__ uint32_t s_idx[BSW_WARPS][BSW_MAX], s_grp[BSW_WARPS][BSW_MAX];
   __shared__ uint8_t s_l[BSW_WARPS][BSW_MAX], s_gl[BSW_WARPS][BSW_MAX];
   __shared__ unsigned s_cnt[BSW_WARPS][64], s_off[BSW_WARPS][64], s_cur[BSW_WARPS][64];
-  const DevCounters *C = B.ctr;
+  DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
   const int cur = (int)(C->step & 1);
@@ -647,6 +649,11 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     const int g = B.occ_list[o];
     const unsigned S0 = B.brick_start[g], m = B.brick_count[g];
     if (m > BSW_MAX) continue;  // warp-uniform: k_brick_sort's brick
+    if (lane == 0 && m >= FORCE_HEAVY_LO) {
+      // heavy bricks (below FORCE_HEAVY_HI here), listed for the force
+      // kernels' largest-first order
+      B.heavy[B.occ_cap - 1 - (long long)atomicAdd(&C->heavy_n[1], 1ull)] = (int32_t)o;
+    }
     s_cnt[w][lane] = 0u;
     s_cnt[w][lane + 32] = 0u;
     __syncwarp();
