@@ -576,12 +576,6 @@ __device__ __forceinline__ float contact_df(const DevParams &P, const dbl4 &pq, 
   return fabsf(Ff);
 }
 
-// The same, out of line (for the force kernel's rare use, so that its main
-// loop keeps its registers).
-__device__ __noinline__ float contact_int_call(const dbl4 &pq, const dbl4 &pc, int fs, float k, float gamma, float &fx,
-                                               float &fy, float &fz) {
-  return contact_int(pq, pc, fs, k, gamma, fx, fy, fz);
-}
 
 // FP32 force of a certain contact at squared distance d2 (s = r_i + r_j, pi =
 // r_i r_j): overlap delta, the scale F / d of the difference vector, and the
@@ -1859,35 +1853,24 @@ __global__ void k_reset_work(DevBufs B) {
 }
 
 // ---------------------------------------------------------------- fix-up pass (FP32 form)
-// The FP32-form agents that the force kernel listed (an FP32 error bound not
-// small against the agent's tolerance, or a summed pair-force magnitude so
-// small that the absolute floor dominates) are evaluated again here, one warp
-// per agent: the lanes walk the agent's 27-box stencil.  A pair the FP32
-// bands cannot decide (cutoff or contact) goes to the warp's list of FP64
-// pairs; a contact whose force magnitude is below low_scale (near the sign
-// change of k delta - gamma sqrt(rbar delta)) takes the double-float
-// arithmetic of contact_df; a grazing contact (delta < graze) and a close pair
-// (d^2 < close2) take the exact-integer geometry of contact_int; the other
-// contacts are summed exactly as the force kernel does.  The list is evaluated
-// in FP64 32 pairs per warp instruction (an FP64 instruction costs GB300's slow
-// FP64 pipe as much for one active lane as for 32) and summed in list order.
-// The sum, rounded to FP32, goes through the force kernel's epilogue
-// (displacement, behaviours, flags, bounding box), or to the debug outputs in
-// FM_FORCES; the neighbour and contact counts are the force kernel's.
-#define FIX_WARPS 8
-#define FIX_BATCH 4   // candidates per lane whose loads are in flight together
-#define FIX_PAIRS 64  // FP64 pairs a warp's list holds (evaluated when full)
+// The FP32-form agents that the lane-per-agent force kernel listed (an FP32
+// error bound not small against the agent's tolerance, or a summed pair-force
+// magnitude so small that the absolute floor dominates) are evaluated again
+// here, one thread per listed agent: each thread walks its agent's 27-box
+// stencil in the canonical order, with k_force's FP32
+// prefilter and decisions (FP64 inside the error bands); every contact the
+// FP32 error analysis does not cover (|F| < low_scale, delta < graze, d^2 <
+// close2) in double-float (contact_df), the others with the force kernel's
+// FP32 arithmetic; the contributions summed in FP64, rounded to FP32 once.
+// The listed agents are few (1-2% of a dense tissue), so each warp's lanes
+// are independent agents and no warp work is spent on an agent's stencil set-up.
+#define FIXT_THREADS 128
 template <int MODE>
-__global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevParams P) {
-  __shared__ unsigned s_pre[FIX_WARPS][28], s_st[FIX_WARPS][28];
-  __shared__ unsigned long long s_bb[FIX_WARPS][6];
+__global__ void __launch_bounds__(FIXT_THREADS, 6) k_force_fix(DevBufs B, DevParams P) {
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
   __shared__ DF s_tk2[16], s_tg2[16];
-  __shared__ float4 s_fc[FIX_WARPS][FIX_BATCH][32];
-  __shared__ unsigned s_fk[FIX_WARPS][FIX_BATCH][32];
-  __shared__ uint8_t s_fb[FIX_WARPS][FIX_BATCH][32];
-  __shared__ unsigned s_pk[FIX_WARPS][FIX_PAIRS];  // the list: candidates' sorted indices
+  __shared__ unsigned long long s_bb[FIXT_THREADS / 32][6];
   DevCounters *C = B.ctr;
   if (C->error) return;
   const unsigned long long nfix = C->fix_n;
@@ -1901,188 +1884,97 @@ __global__ void __launch_bounds__(FIX_WARPS * 32) k_force_fix(DevBufs B, DevPara
     s_tk2[threadIdx.x] = {kh, (float)(P.type_k[threadIdx.x] - (double)kh)};
     s_tg2[threadIdx.x] = {gh, (float)(P.type_gamma[threadIdx.x] - (double)gh)};
   }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
   __syncthreads();
   const AgentSet A = *B.A;
   const int cur = (int)(C->step & 1), nxt = cur ^ 1;
   const long long step = C->step;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane < 6) s_bb[warp][lane] = (lane < 3) ? ~0ull : 0ull;
-  __syncwarp();
   unsigned c_static = 0, c_moved = 0, n_exact = 0;
   int wsim = -1;
-  const unsigned lt = (1u << lane) - 1u;  // lanes below this one
-  for (unsigned long long e = (unsigned long long)blockIdx.x * FIX_WARPS + warp; e < nfix;
-       e += (unsigned long long)gridDim.x * FIX_WARPS) {
-    if (!BDM_IN(B.ctr, (long long)e < B.cap)) break;
-    const uint4 ent = B.fix[e];
+  // warp-uniform trip count (the bounding-box flushes are warp-wide)
+  const unsigned long long stride = (unsigned long long)gridDim.x * FIXT_THREADS;
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * FIXT_THREADS + (threadIdx.x & ~31u); e0 < nfix;
+       e0 += stride) {
+    const unsigned long long e = e0 + (unsigned long long)lane;
+    bool valid = e < nfix && BDM_IN(B.ctr, (long long)e < B.cap);
+    const uint4 ent = valid ? B.fix[e] : make_uint4(0u, 0u, 0u, 0u);
     const unsigned kq = ent.x;
     const long long o = (long long)(ent.y >> 6);
     const int lb = (int)(ent.y & 63u);
-    if (!BDM_IN(B.ctr, o < C->n_occ && (long long)kq < C->n)) continue;
-    const int4 info = B.occ_info[o];
-    const SimGeom &G = B.geom[info.w];
-    if (MODE == FM_STEP && info.w != wsim) {
-      flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
-      wsim = info.w;
+    if (valid && !BDM_IN(B.ctr, o < C->n_occ && (long long)kq < C->n)) valid = false;
+    const int4 info = valid ? B.occ_info[o] : make_int4(0, 0, 0, 0);
+    // the warp's bounding-box accumulator holds one simulation at a time; a
+    // warp whose agents belong to several simulations updates each agent's
+    // simulation box directly
+    bool same = true;
+    if (MODE == FM_STEP) {
+      const int sim0 = __shfl_sync(0xffffffffu, valid ? info.w : -1, 0);
+      same = __all_sync(0xffffffffu, !valid || info.w == sim0);
+      if (same && sim0 != wsim) {
+        flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
+        wsim = sim0;
+      }
     }
-    // the 27 stencil boxes (canonical order) and their agent ranges
-    int lx, ly, lz;
-    local_decode(lb, lx, ly, lz);
-    unsigned nb_st = 0, nb_cnt = 0;
-    if (lane < 27) {
-      const int ax = lx + lane % 3 - 1, ay = ly + (lane / 3) % 3 - 1, az = lz + lane / 9 - 1;
-      const int X = info.x + ((ax < 0) ? -1 : (ax > 3 ? 1 : 0));
-      const int Y = info.y + ((ay < 0) ? -1 : (ay > 3 ? 1 : 0));
-      const int Z = info.z + ((az < 0) ? -1 : (az > 3 ? 1 : 0));
-      if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
+    double hx = 0.0, hy = 0.0, hz = 0.0;
+    if (valid) {
+      const SimGeom &G = B.geom[info.w];
+      const float4 cq = B.c32[kq];
+      const dbl4 dq = exact_of<1>(B, A, cur, kq);
+      const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;
+      int lx, ly, lz;
+      local_decode(lb, lx, ly, lz);
+      for (int sb = 0; sb < 27; ++sb) {
+        const int ax = lx + sb % 3 - 1, ay = ly + (sb / 3) % 3 - 1, az = lz + sb / 9 - 1;
+        const int X = info.x + ((ax < 0) ? -1 : (ax > 3 ? 1 : 0));
+        const int Y = info.y + ((ay < 0) ? -1 : (ay > 3 ? 1 : 0));
+        const int Z = info.z + ((az < 0) ? -1 : (az > 3 ? 1 : 0));
+        if (X < 0 || X >= G.nr[0] || Y < 0 || Y >= G.nr[1] || Z < 0 || Z >= G.nr[2]) continue;
         const int rank = B.brick_table[G.brick_base + ((long long)Z * G.nr[1] + Y) * G.nr[0] + X];
         const int occ = B.brick_occ[rank];
-        if (occ >= 0) {
-          const int lc = local_code(ax & 3, ay & 3, az & 3);
-          nb_st = B.box_start[(long long)occ * 64 + lc];
-          nb_cnt = B.box_cnt[(long long)occ * 64 + lc];
-        }
-      }
-    }
-    unsigned pre = nb_cnt;
-    for (int of = 1; of < 32; of <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, pre, of);
-      if (lane >= of) pre += y;
-    }
-    const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
-    if (lane < 27) {
-      s_pre[warp][lane] = pre - nb_cnt;
-      s_st[warp][lane] = nb_st;
-    }
-    __syncwarp();
-    const float4 cq = B.c32[kq];
-    const dbl4 dq = exact_of<1>(B, A, cur, kq);
-    const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;
-    double hx = 0.0, hy = 0.0, hz = 0.0;  // this lane's FP64 pairs
-    float gx = 0.f, gy = 0.f, gz = 0.f;   // this lane's FP32 contacts
-    unsigned np = 0;                      // pairs in the list (warp-uniform)
-    // evaluate the listed FP64 pairs, 32 per warp instruction
-    auto flush_pairs = [&]() {
-      for (unsigned p0 = 0; p0 < np; p0 += 32) {
-        if (p0 + lane < np) {
-          const unsigned kj = s_pk[warp][p0 + lane];
+        if (occ < 0) continue;
+        const long long bx = (long long)occ * 64 + local_code(ax & 3, ay & 3, az & 3);
+        const unsigned st = B.box_start[bx], cnt = B.box_cnt[bx];
+        const float ofx = (float)(sb % 3 - 1) * P.Lf, ofy = (float)((sb / 3) % 3 - 1) * P.Lf,
+                    ofz = (float)(sb / 9 - 1) * P.Lf;
+        for (unsigned j = 0; j < cnt; ++j) {
+          const unsigned kj = st + j;
+          if (!BDM_IN(B.ctr, (long long)kj < C->n)) break;
+          const float4 cs = __ldg(&B.c32[kj]);
+          const float4 c = make_float4(cs.x + ofx, cs.y + ofy, cs.z + ofz, cs.w);
+          const float d2 = dist2_f32(cq, c);
+          if (!(d2 < P.R2_hi_f) || kj == kq) continue;
+          const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
+          const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
+          const float W = fmaf(s, P.cband1, s2 * P.cband2);
+          if (!band && d2 >= s2 + W) continue;  // a neighbour, certainly no contact
           const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
-          pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, exact_of<1>(B, A, cur, kj), hx, hy, hz);
           n_exact++;
-        }
-      }
-      np = 0;
-      __syncwarp();
-    };
-    for (unsigned p0 = 0; p0 < ctot; p0 += 32u * FIX_BATCH) {
-      // FIX_BATCH candidates per lane: their loads in flight together, the
-      // records kept in shared memory for the classification loop
-      {
-        unsigned kjv[FIX_BATCH];
-        int bxv[FIX_BATCH];
-        float4 cv[FIX_BATCH];
-#pragma unroll
-        for (int u = 0; u < FIX_BATCH; ++u) {
-          const unsigned p = p0 + lane + 32u * u;
-          int bx = 0;
-          for (int st = 16; st > 0; st >>= 1)
-            if (bx + st <= 26 && s_pre[warp][bx + st] <= p) bx += st;
-          bxv[u] = bx;
-          kjv[u] = s_st[warp][bx] + (p - s_pre[warp][bx]);
-        }
-#pragma unroll
-        for (int u = 0; u < FIX_BATCH; ++u)
-          if (p0 + lane + 32u * u < ctot) cv[u] = __ldg(&B.c32[kjv[u]]);
-#pragma unroll
-        for (int u = 0; u < FIX_BATCH; ++u) {
-          s_fc[warp][u][lane] = cv[u];
-          s_fk[warp][u][lane] = kjv[u];
-          s_fb[warp][u][lane] = (uint8_t)bxv[u];
-        }
-      }
-      for (int u = 0; u < FIX_BATCH; ++u) {
-        if (p0 + 32u * u >= ctot) break;  // warp-uniform
-        bool risky = false;
-        unsigned kj = 0;
-        if (p0 + lane + 32u * u < ctot) {
-          kj = s_fk[warp][u][lane];
-          const int bx = (int)s_fb[warp][u][lane];
-          const float4 c = s_fc[warp][u][lane];
-          if (kj != kq && BDM_IN(B.ctr, (long long)kj < C->n)) {
-            const float ofx = (float)(bx % 3 - 1) * P.Lf, ofy = (float)((bx / 3) % 3 - 1) * P.Lf,
-                        ofz = (float)(bx / 9 - 1) * P.Lf;
-            const float ex = __fsub_rn(cq.x, __fadd_rn(c.x, ofx)), ey = __fsub_rn(cq.y, __fadd_rn(c.y, ofy)),
-                        ez = __fsub_rn(cq.z, __fadd_rn(c.z, ofz));
-            const float d2 = fmaf(ex, ex, fmaf(ey, ey, __fmul_rn(ez, ez)));
-            if (d2 < P.R2_hi_f) {  // else certainly no neighbour
-              const float s = __fadd_rn(cq.w, c.w), s2 = s * s;
-              const float W = fmaf(s, P.cband1, s2 * P.cband2);
-              const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
-              if (band || d2 < s2 + W) {  // else a neighbour, certainly no contact
-                // the cutoff or the contact undecided in FP32: FP64 (list)
-                risky = band || d2 > s2 - W;
-                if (!risky) {
-                  // a certain contact: the force kernel's FP32 arithmetic, or
-                  // where that is too coarse: a force magnitude below
-                  // low_scale sits near the root of k delta = gamma
-                  // sqrt(rbar delta), where an FP32 delta's rounding (about
-                  // k/2 delta eps) is not small against the absolute floor
-                  // (double-float, contact_df); a grazing or close contact
-                  // needs the exact geometry (contact_int)
-                  const int ab = tq4 + ((P.n_types > 1) ? (int)B.tp[kj] : 0);
-                  const ContactF32 k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
-                  if (fabsf(k.fm) < P.low_scale) {
-                    float tx, ty, tz;
-                    contact_df(P, dq, exact_of<1>(B, A, cur, kj), s_tk2[ab], s_tg2[ab], tx, ty, tz);
-                    hx += (double)tx;
-                    hy += (double)ty;
-                    hz += (double)tz;
-                    n_exact++;
-                  } else if (k.delta < P.graze || d2 < P.close2) {
-                    float tx, ty, tz;
-                    contact_int(dq, exact_of<1>(B, A, cur, kj), P.fix_shift, s_tkf[ab], s_tgf[ab], tx, ty, tz);
-                    hx += (double)tx;
-                    hy += (double)ty;
-                    hz += (double)tz;
-                    n_exact++;
-                  } else {
-                    gx = fmaf(k.scf, ex, gx);
-                    gy = fmaf(k.scf, ey, gy);
-                    gz = fmaf(k.scf, ez, gz);
-                  }
-                }
-              }
-            }
+          if (band || d2 > s2 - W) {  // cutoff or contact undecided in FP32: FP64
+            pair_f64_k(P.R2, s_tkd[ab], s_tgd[ab], dq, exact_of<1>(B, A, cur, kj), hx, hy, hz);
+            continue;
+          }
+          const ContactF32 k = contact_f32(d2, s, __fmul_rn(cq.w, c.w), s_tkf[ab], s_tgf[ab]);
+          if (fabsf(k.fm) < P.low_scale || k.delta < P.graze || d2 < P.close2) {
+            float tx, ty, tz;
+            contact_df(P, dq, exact_of<1>(B, A, cur, kj), s_tk2[ab], s_tg2[ab], tx, ty, tz);
+            hx += (double)tx; hy += (double)ty; hz += (double)tz;
+          } else {
+            n_exact--;
+            hx += (double)__fmul_rn(k.scf, __fsub_rn(cq.x, c.x));
+            hy += (double)__fmul_rn(k.scf, __fsub_rn(cq.y, c.y));
+            hz += (double)__fmul_rn(k.scf, __fsub_rn(cq.z, c.z));
           }
         }
-        // append this step's FP64 pairs to the list (lane order), evaluating
-        // the list first when they would not fit
-        const unsigned bal = __ballot_sync(0xffffffffu, risky);
-        const unsigned cnt = __popc(bal);
-        if (np + cnt > FIX_PAIRS) flush_pairs();
-        if (risky) s_pk[warp][np + __popc(bal & lt)] = kj;
-        np += cnt;
-        __syncwarp();
       }
-    }
-    flush_pairs();
-    hx += (double)gx;
-    hy += (double)gy;
-    hz += (double)gz;
-    for (int of = 16; of > 0; of >>= 1) {
-      hx += __shfl_xor_sync(0xffffffffu, hx, of);
-      hy += __shfl_xor_sync(0xffffffffu, hy, of);
-      hz += __shfl_xor_sync(0xffffffffu, hz, of);
-    }
-    if (lane == 0) {
       const uint32_t iq = B.perm[kq];
       double px = 0.0, py = 0.0, pz = 0.0;
       if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }
       // the force kernel's neighbour and contact counts (ent.w, ent.z)
       finish_agent<1, MODE>(B, P, A, cur, nxt, step, G.dt, G.dt_f, iq, A.flags[iq], false, (float)hx, (float)hy,
-                            (float)hz, 0.0, 0.0, 0.0, ent.w, ent.z, c_static, c_moved, s_bb[warp], px, py, pz);
+                            (float)hz, 0.0, 0.0, 0.0, ent.w, ent.z, c_static, c_moved,
+                            same ? s_bb[warp] : B.bbox + ((size_t)nxt * P.n_sims + info.w) * 6, px, py, pz);
     }
-    __syncwarp();
   }
   if (MODE == FM_STEP) flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
   const unsigned long long t_moved = wsum64(c_moved), t_exact = wsum64(n_exact);
@@ -2419,8 +2311,8 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
 void launch_force_fix(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int mode, cudaStream_t s) {
   // the tiled and sparse kernels list no agent
   if (P.precision != 1 || P.lanes_fixed == FORCE_TILE || P.lanes_fixed == FORCE_SPARSE) return;
-  if (mode == FM_STEP) k_force_fix<FM_STEP><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
-  if (mode == FM_FORCES) k_force_fix<FM_FORCES><<<c.occ_blocks, FIX_WARPS * 32, 0, s>>>(B, P);
+  if (mode == FM_STEP) k_force_fix<FM_STEP><<<2 * c.occ_blocks, FIXT_THREADS, 0, s>>>(B, P);
+  if (mode == FM_FORCES) k_force_fix<FM_FORCES><<<2 * c.occ_blocks, FIXT_THREADS, 0, s>>>(B, P);
 }
 
 int force_launches(const DevParams &P) { (void)P; return 2; }
