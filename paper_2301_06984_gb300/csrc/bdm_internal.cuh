@@ -254,6 +254,51 @@ __device__ __forceinline__ void local_decode(int c, int &lx, int &ly, int &lz) {
   lz = ((c >> 2) & 1) | ((c >> 4) & 2);
 }
 
+// The 27-box stencil of a local box as masks over the bricks around its
+// brick: for local box lb, up to 8 (brick, 64-bit box mask) pairs; bo is the
+// brick's index among the 27 ((dz + 1) 9 + (dy + 1) 3 + (dx + 1)).  A box is
+// dirty when some pair's mask meets that brick's dirty mask.  The table is
+// built at compile time (the same Morton code as local_code).
+struct StencilMasks {
+  unsigned long long m[64][8];
+  unsigned char b[64][8];
+  unsigned char n[64];
+};
+constexpr StencilMasks make_stencil_masks() {
+  StencilMasks S{};
+  for (int lb = 0; lb < 64; ++lb) {
+    const int lx = (lb & 1) | ((lb >> 2) & 2), ly = ((lb >> 1) & 1) | ((lb >> 3) & 2),
+              lz = ((lb >> 2) & 1) | ((lb >> 4) & 2);
+    int n = 0;
+    for (int t = 0; t < 27; ++t) {
+      const int ax = lx + t % 3 - 1, ay = ly + (t / 3) % 3 - 1, az = lz + t / 9 - 1;
+      const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                     ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+      const int x = ax & 3, y = ay & 3, z = az & 3;
+      const int code = (x & 1) | ((y & 1) << 1) | ((z & 1) << 2) | ((x & 2) << 2) | ((y & 2) << 3) | ((z & 2) << 4);
+      int e = 0;
+      while (e < n && S.b[lb][e] != bo) ++e;
+      if (e == n) {
+        S.b[lb][e] = (unsigned char)bo;
+        ++n;
+      }
+      S.m[lb][e] |= 1ull << code;
+    }
+    S.n[lb] = (unsigned char)n;
+  }
+  return S;
+}
+__device__ const StencilMasks g_stencil_masks = make_stencil_masks();
+// whether a box of the stencil of local box lb is dirty (dm: the 27 bricks'
+// dirty masks)
+__device__ __forceinline__ bool stencil_dirty(const unsigned long long *dm, int lb) {
+  const StencilMasks &S = g_stencil_masks;
+  unsigned long long any = 0ull;
+  const int n = __ldg(&S.n[lb]);
+  for (int e = 0; e < n; ++e) any |= dm[__ldg(&S.b[lb][e])] & __ldg(&S.m[lb][e]);
+  return any != 0ull;
+}
+
 __device__ __forceinline__ int sim_of_agent(const long long *sim_off, int n_sims, long long i) {
   int lo = 0, hi = n_sims - 1;
   while (lo < hi) {

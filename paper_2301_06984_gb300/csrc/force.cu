@@ -1464,10 +1464,11 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
 // FP32 form, FM_STEP and FM_FORCES (lanes = -3), for sparse tissue: boxes of
 // one to a few agents (a shell around a static core, the small simulations of
 // an ensemble), where the per-box work of the box-per-warp kernels (stencil
-// set-up, staging, lists) is shared by too few agents.  One CTA per occupied
-// brick (heaviest first, the static pass's work list as in k_force); its
-// threads take the agents of its boxes with work one per lane, in rounds of
-// the CTA size, and each lane walks its own agent's 27-box stencil in the canonical order,
+// set-up, staging, lists) is shared by too few agents.  One warp per occupied
+// brick (heaviest first, the static pass's work list as in k_force; no block
+// barriers); its lanes take the agents of the brick's boxes with work one per
+// lane, in rounds of 32, and each lane walks its own agent's 27-box stencil in
+// the canonical order,
 // testing every candidate with k_force's FP32 prefilter and deciding
 // neighbour and contact exactly as k_force does (FP32 outside the error
 // bands, FP64 in place inside them).  A contact the FP32 error analysis covers
@@ -1481,17 +1482,17 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
 template <int MODE, bool TYPES>
 __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, DevParams P) {
   static_assert(MODE == FM_STEP || MODE == FM_FORCES, "the sparse kernel computes forces");
-  __shared__ int s_nocc[27];
-  __shared__ unsigned long long s_ndirty[27];
-  __shared__ unsigned s_bst[65];                  // the brick's box starts and its end
-  __shared__ unsigned long long s_need, s_clean;  // boxes with work; boxes with a clean stencil
-  __shared__ long long s_o;
+  // per warp: its brick's 27 neighbour bricks (occupied index, dirty mask),
+  // box starts (and end), and the agents of boxes with work before each box
+  __shared__ int s_nocc[SP_WARPS][27];
+  __shared__ unsigned long long s_ndirty[SP_WARPS][27];
+  __shared__ unsigned s_bst[SP_WARPS][65];
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[SP_WARPS][6];
   __shared__ uint32_t s_dq[SP_WARPS][SP_Q][32];   // each lane's queued candidates (sorted positions)
   __shared__ float4 s_dr[SP_WARPS][SP_Q][32];     // and their double-float forces
   __shared__ uint32_t s_dk[SP_WARPS][32];         // each lane's agent (sorted position)
-  __shared__ unsigned s_ncum[65];                 // agents of boxes with work before each box
+  __shared__ unsigned s_ncum[SP_WARPS][65];
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
   __shared__ DF s_tk2[16], s_tg2[16];
@@ -1522,18 +1523,20 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
   }
   unsigned n_cand = 0, n_nbr = 0, n_cont = 0, n_exact = 0;  // this thread's statistics
 
+  __syncthreads();  // the block's tables are written
+  // one brick per warp (taken from the global brick order): no block barriers,
+  // so a warp on a brick with few agents to compute does not hold the others
   while (true) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
-    __syncthreads();
-    const long long o = s_o;
+    long long o = 0;
+    if (lane == 0) o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+    o = __shfl_sync(0xffffffffu, o, 0);
     if (o < 0) break;
-    if (!BDM_IN(B.ctr, o < n_occ)) break;  // block-uniform
+    if (!BDM_IN(B.ctr, o < n_occ)) break;  // warp-uniform
     const int4 info = B.occ_info[o];
     const SimGeom &G = B.geom[info.w];
-    if (threadIdx.x < 27) {
-      const int t = threadIdx.x;
-      const int X = info.x + t % 3 - 1, Y = info.y + (t / 3) % 3 - 1, Z = info.z + t / 9 - 1;
+    __syncwarp();  // the previous brick's readers of the warp's tables are done
+    if (lane < 27) {
+      const int X = info.x + lane % 3 - 1, Y = info.y + (lane / 3) % 3 - 1, Z = info.z + lane / 9 - 1;
       int occ = -1;
       unsigned long long dm = 0ull;
       if (X >= 0 && X < G.nr[0] && Y >= 0 && Y < G.nr[1] && Z >= 0 && Z < G.nr[2]) {
@@ -1541,67 +1544,58 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
         occ = B.brick_occ[rank];
         if (use_static) dm = B.dirty[rank];
       }
-      s_nocc[t] = occ;
-      s_ndirty[t] = dm;
+      s_nocc[warp][lane] = occ;
+      s_ndirty[warp][lane] = dm;
     }
-    if (threadIdx.x >= 32 && threadIdx.x < 96) s_bst[threadIdx.x - 32] = B.box_start[o * 64 + threadIdx.x - 32];
-    if (threadIdx.x == 96) {
-      s_need = use_static ? B.need[o] : ~0ull;
-      s_bst[64] = B.box_start[o * 64 + 63] + B.box_cnt[o * 64 + 63];
-      s_clean = 0ull;
+    s_bst[warp][lane] = B.box_start[o * 64 + lane];
+    s_bst[warp][lane + 32] = B.box_start[o * 64 + lane + 32];
+    if (lane == 0) s_bst[warp][64] = B.box_start[o * 64 + 63] + B.box_cnt[o * 64 + 63];
+    const unsigned long long need = use_static ? B.need[o] : ~0ull;  // boxes with work
+    __syncwarp();
+    // boxes with a clean stencil (no dirty box in it)
+    unsigned long long clean = 0ull;
+    if (use_static) {
+      const bool c0 = !stencil_dirty(s_ndirty[warp], lane), c1 = !stencil_dirty(s_ndirty[warp], lane + 32);
+      clean = (unsigned long long)__ballot_sync(0xffffffffu, c0) |
+              ((unsigned long long)__ballot_sync(0xffffffffu, c1) << 32);
     }
-    __syncthreads();
-    if (use_static && threadIdx.x < 64) {
-      // a box is clean when no box of its 27-box stencil is dirty
-      int lx, ly, lz;
-      local_decode((int)threadIdx.x, lx, ly, lz);
-      bool dirty = false;
-      for (int t = 0; t < 27; ++t) {
-        const int ax = lx + t % 3 - 1, ay = ly + (t / 3) % 3 - 1, az = lz + t / 9 - 1;
-        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
-                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
-        dirty |= (s_ndirty[bo] >> local_code(ax & 3, ay & 3, az & 3)) & 1ull;
-      }
-      if (!dirty) atomicOr(&s_clean, 1ull << threadIdx.x);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
+    {
       // exclusive prefix of the agent counts of the boxes with work (two
       // boxes per lane)
-      const int l2 = 2 * (int)threadIdx.x;
-      const unsigned a0 = ((s_need >> l2) & 1ull) ? s_bst[l2 + 1] - s_bst[l2] : 0u;
-      const unsigned a1 = ((s_need >> (l2 + 1)) & 1ull) ? s_bst[l2 + 2] - s_bst[l2 + 1] : 0u;
+      const int l2 = 2 * lane;
+      const unsigned a0 = ((need >> l2) & 1ull) ? s_bst[warp][l2 + 1] - s_bst[warp][l2] : 0u;
+      const unsigned a1 = ((need >> (l2 + 1)) & 1ull) ? s_bst[warp][l2 + 2] - s_bst[warp][l2 + 1] : 0u;
       unsigned inc = a0 + a1;
       for (int of = 1; of < 32; of <<= 1) {
         const unsigned y = __shfl_up_sync(0xffffffffu, inc, of);
-        if ((int)threadIdx.x >= of) inc += y;
+        if (lane >= of) inc += y;
       }
-      s_ncum[l2] = inc - a0 - a1;
-      s_ncum[l2 + 1] = inc - a1;
-      if (threadIdx.x == 31) s_ncum[64] = inc;
+      s_ncum[warp][l2] = inc - a0 - a1;
+      s_ncum[warp][l2 + 1] = inc - a1;
+      if (lane == 31) s_ncum[warp][64] = inc;
     }
-    __syncthreads();
+    __syncwarp();
     if (MODE == FM_STEP && info.w != wsim) {
       flush_bbox_warp(B, P, nxt, wsim, s_bb[warp]);
       wsim = info.w;
     }
     const double dt = G.dt;
     const float dt_f = G.dt_f;
-    const unsigned nw = s_ncum[64];  // agents of the brick's boxes with work
-    // rounds of one agent per thread (CTA-uniform trip count)
-    for (unsigned r0 = 0; r0 < nw; r0 += SP_WARPS * 32) {
-      const unsigned i = r0 + threadIdx.x;
+    const unsigned nw = s_ncum[warp][64];  // agents of the brick's boxes with work
+    // rounds of one agent per lane (warp-uniform trip count)
+    for (unsigned r0 = 0; r0 < nw; r0 += 32u) {
+      const unsigned i = r0 + (unsigned)lane;
       bool valid = i < nw;
       int lb = 0;  // the agent's box: the last box with work whose first agent is at or before i
 #pragma unroll
       for (int st = 32; st > 0; st >>= 1)
-        if (lb + st < 64 && s_ncum[lb + st] <= i) lb += st;
-      const unsigned kq = valid ? s_bst[lb] + (i - s_ncum[lb]) : s_bst[0];
+        if (lb + st < 64 && s_ncum[warp][lb + st] <= i) lb += st;
+      const unsigned kq = valid ? s_bst[warp][lb] + (i - s_ncum[warp][lb]) : s_bst[warp][0];
       if (!BDM_IN(B.ctr, !valid || (long long)kq < C->n)) valid = false;
       uint32_t iq = valid ? B.perm[kq] : 0u;
       if (!BDM_IN(B.ctr, (long long)iq < B.cap)) { iq = 0; valid = false; }
       const uint8_t fl = valid ? A.flags[iq] : (uint8_t)0;
-      const bool is_static = use_static && valid && ((s_clean >> lb) & 1ull) && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
+      const bool is_static = use_static && valid && ((clean >> lb) & 1ull) && !(fl & FL_CHANGED) && A.nz[iq] <= 1;
       const bool compute = valid && !is_static;
       const float4 cq = B.c32[kq];
       const int tq4 = TYPES ? 4 * (int)B.tp[kq] : 0;
@@ -1615,7 +1609,7 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
           const int ax = lx + sb % 3 - 1, ay = ly + (sb / 3) % 3 - 1, az = lz + sb / 9 - 1;
           const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
                          ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
-          const int occ = s_nocc[bo];
+          const int occ = s_nocc[warp][bo];
           if (occ < 0) continue;
           const long long bx = (long long)occ * 64 + local_code(ax & 3, ay & 3, az & 3);
           const unsigned st = B.box_start[bx], cnt = B.box_cnt[bx];
@@ -1790,15 +1784,7 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P
     unsigned long long cm = 0ull;
     for (int h = 0; h < 2; ++h) {
       const int lb = lane + 32 * h;
-      int lx, ly, lz;
-      local_decode(lb, lx, ly, lz);
-      bool dirty = false;
-      for (int t = 0; t < 27; ++t) {
-        const int ax = lx + t % 3 - 1, ay = ly + (t / 3) % 3 - 1, az = lz + t / 9 - 1;
-        const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
-                       ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
-        dirty |= ((s_dm[w][bo] >> local_code(ax & 3, ay & 3, az & 3)) & 1ull) != 0ull;
-      }
+      const bool dirty = stencil_dirty(s_dm[w], lb);
       s_work[w][lb] = dirty ? s_bcnt[w][lb] : 0u;
       cm |= (unsigned long long)__ballot_sync(0xffffffffu, !dirty) << (32 * h);
     }
