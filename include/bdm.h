@@ -235,9 +235,9 @@ int bdm_get_debug(bdm_sim *sim, int what, void *out, int64_t cap, int64_t *n_out
 /* Autotuner.  Times `trial_steps` iterations of the production path (after
  * one warm-up iteration) for each candidate setting, restoring the state
  * before every trial, and keeps the fastest: the box edge L in {R, 1.125 R,
- * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel in {4 lanes per
- * agent, the tiled kernel, the sparse kernel, the per-box cost model}
- * (BDM_TUNE_LANES; the values 4, 0, -3, -1 of bdm_set_force_kernel), and the sort
+ * 1.25 R, 1.5 R} (BDM_TUNE_BOX_EDGE), the FP32-force kernel in {the hybrid
+ * launch, 4 lanes per agent, the sparse kernel, the tiled kernel}
+ * (BDM_TUNE_LANES; the values -4, 4, -3, 0 of bdm_set_force_kernel), and the sort
  * cadence in {current, 0, 5, 10, 20} (BDM_TUNE_SORT), one dimension after the
  * other.  The state (agents, step, uid counter) is the same afterwards; the
  * static-detection history starts empty.  Changing L keeps neighbour sets
@@ -257,22 +257,25 @@ typedef struct {
 int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
 
 /* FP32-force kernel choice (no counterpart in the paper, whose force loop is
- * one thread per agent).  lanes = 1, 2, 4 (the default), 8, 16 or 32 selects
- * the lane-per-agent kernel: a warp takes a box's agents, that many lanes
- * split each agent's candidates, and each lane queues its prefiltered pairs
- * before evaluating them; agents whose FP32 error bound is not small against
- * their tolerance are finished by a fix-up pass.  lanes = -1 selects the same
- * kernel with the lanes chosen per box by a cost model.  lanes = 0 selects the
- * tiled kernel: a warp tests all of a box's agents against each staged chunk
- * of the 27-box stencil (one lane per candidate), collects the pairs that pass
- * in a shared list and evaluates the list 32 pairs per warp instruction.
- * lanes = -3 selects the sparse kernel: one thread per agent walks its own
- * 27-box stencil (for tissue of one to a few agents per box).  The tiled and
- * sparse kernels evaluate every contact the FP32 error analysis does not cover
- * in double-float arithmetic in place, so they need no fix-up pass.  All give
- * the same neighbour and contact decisions (FP64-exact) and forces within the
- * FP32-form tolerance; the choice takes effect at the next iteration.  No
- * effect on the FP64 form.  Errors: BDM_EINVAL (other lanes values). */
+ * one thread per agent).  lanes = 1, 2, 4, 8, 16 or 32 selects the
+ * lane-per-agent kernel: a warp takes a box's agents, that many lanes split
+ * each agent's candidates, and each lane queues its prefiltered pairs before
+ * evaluating them; agents whose FP32 error bound is not small against their
+ * tolerance are finished by a fix-up pass.  lanes = -1 selects the same kernel
+ * with the lanes chosen per box by a cost model.  lanes = 0 selects the tiled
+ * kernel: a warp tests all of a box's agents against each staged chunk of the
+ * 27-box stencil (one lane per candidate), collects the pairs that pass in a
+ * shared list and evaluates the list 32 pairs per warp instruction.  lanes =
+ * -3 selects the sparse kernel: one warp per brick, one lane per agent walking
+ * its own 27-box stencil (for tissue of one to a few agents per box).  The
+ * tiled and sparse kernels evaluate every contact the FP32 error analysis does
+ * not cover in double-float arithmetic in place, so they need no fix-up pass.
+ * lanes = -4 (the default) selects the hybrid launch: the sparse kernel for the
+ * bricks of fewer than 128 agents, the lane-per-agent kernel with 4 lanes for
+ * the others.  All give the same neighbour and contact decisions (FP64-exact)
+ * and forces within the FP32-form tolerance; the choice takes effect at the
+ * next iteration.  No effect on the FP64 form.  Errors: BDM_EINVAL (other lanes
+ * values). */
 int bdm_set_force_kernel(bdm_sim *sim, int lanes);
 
 /* Phase profiling.  After bdm_profile_begin, bdm_step launches each

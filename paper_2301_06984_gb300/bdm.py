@@ -309,12 +309,14 @@ class Simulation:
         self._check(lib().bdm_autotune(self._h, int(trial_steps), int(what), C.byref(t)))
         return {k: getattr(t, k) for k, _ in t._fields_ if k != "reserved"}
 
-    def set_force_kernel(self, lanes=4):
-        """FP32 form: 1, 2, 4 (the default), 8, 16, 32 = the lane-per-agent
-        kernel with that many lanes per agent; -1 = the same with the lanes
-        chosen per box by its cost model; 0 = the tiled kernel; -3 = the sparse
-        kernel (the last two evaluate the contacts the FP32 error analysis does
-        not cover in double-float in place, with no fix-up pass)."""
+    def set_force_kernel(self, lanes=-4):
+        """FP32 form: -4 = the hybrid launch (the default: the sparse kernel for
+        bricks of fewer than 128 agents, 4 lanes per agent for the others);
+        1, 2, 4, 8, 16, 32 = the lane-per-agent kernel with that many lanes per
+        agent; -1 = the same with the lanes chosen per box by its cost model;
+        0 = the tiled kernel; -3 = the sparse kernel (the last two evaluate the
+        contacts the FP32 error analysis does not cover in double-float in
+        place, with no fix-up pass)."""
         self._check(lib().bdm_set_force_kernel(self._h, int(lanes)))
 
     # ------------------------------------------------------------------ profiling

@@ -94,6 +94,7 @@ struct DevCounters {
   long long need_bricks, need_occ;
   int32_t sort_now, force_sort;
   unsigned long long work_next;  // dynamic brick fetch of the force kernel
+  unsigned long long work_next2; // the same for the light bricks of the hybrid force launch
   // the force kernels take the heaviest bricks first: bricks of at least
   // FORCE_HEAVY_HI agents (heavy list front), then of at least FORCE_HEAVY_LO
   // (heavy list back), then the rest in Morton order
@@ -134,6 +135,8 @@ struct DevParams {
                                     // in FP64 (their FP32 direction is too rough)
   int32_t fix_shift;                // fixed-point scale bits of the local coordinates
   int32_t df_shift;                 // fixed-point bits of contact_df's differences (|D| 2^s < 2^46)
+  int32_t brick_class;              // bricks a force launch takes: 0 all, 1 not light, 2 light only
+  uint32_t light_max;               // hybrid force launch: bricks of fewer agents are light
   long long L_fix;                  // box edge in fixed point (multiple of 128)
   int32_t precision, detect_static, sort_every, n_sims, keep_forces, grow, walk, die;
   int32_t n_types;                  // > 1: the pair's constants are type_k / type_gamma[4 a + b]
@@ -369,12 +372,15 @@ struct LaunchCfg {
 
 // FP32 force kernel choice (DevParams::lanes_fixed): FORCE_TILE selects the
 // tiled kernel (k_force_tile), FORCE_SPARSE the sparse kernel
-// (k_force_sparse), a positive value the lane-per-agent kernel with that many
-// lanes per agent, -1 the lane-per-agent kernel with the lanes chosen per box.
-// The default: 4 lanes per agent (fastest on dense tissue)
-#define FORCE_LANES_DEFAULT 4
+// (k_force_sparse), FORCE_HYBRID the sparse kernel for light bricks and the
+// lane-per-agent kernel (4 lanes) for the others, a positive value the
+// lane-per-agent kernel with that many lanes per agent, -1 the lane-per-agent
+// kernel with the lanes chosen per box.  The default: the hybrid launch
 #define FORCE_TILE 0
 #define FORCE_SPARSE (-3)
+#define FORCE_HYBRID (-4)  // the sparse kernel for light bricks, 4 lanes per agent for the others
+#define FORCE_LIGHT_MAX 128
+#define FORCE_LANES_DEFAULT FORCE_HYBRID
 
 // brick weight classes of the force kernels' largest-first order (agents)
 #define FORCE_HEAVY_HI 1024

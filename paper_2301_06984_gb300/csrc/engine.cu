@@ -756,9 +756,9 @@ static int apply_params(bdm_sim *s, const bdm_params &P, int lanes) {
 
 int bdm_set_force_kernel(bdm_sim *s, int lanes) {
   if (!s) return BDM_EINVAL;
-  if (!(lanes == FORCE_SPARSE || lanes == -1 || lanes == FORCE_TILE || lanes == 1 || lanes == 2 || lanes == 4 ||
-        lanes == 8 || lanes == 16 || lanes == 32))
-    return fail(s, BDM_EINVAL, "lanes must be -3, -1, 0, 1, 2, 4, 8, 16 or 32");
+  if (!(lanes == FORCE_HYBRID || lanes == FORCE_SPARSE || lanes == -1 || lanes == FORCE_TILE || lanes == 1 ||
+        lanes == 2 || lanes == 4 || lanes == 8 || lanes == 16 || lanes == 32))
+    return fail(s, BDM_EINVAL, "lanes must be -4, -3, -1, 0, 1, 2, 4, 8, 16 or 32");
   return apply_params(s, s->P, lanes);
 }
 
@@ -840,7 +840,7 @@ int bdm_autotune(bdm_sim *s, int trial_steps, int what, bdm_tuning *out) {
       }
     }
     if (rc == BDM_OK && (what & BDM_TUNE_LANES) && base.precision == BDM_FP32_FORCE) {
-      const int opts[4] = {FORCE_LANES_DEFAULT, FORCE_TILE, FORCE_SPARSE, -1};
+      const int opts[4] = {FORCE_LANES_DEFAULT, 4, FORCE_SPARSE, FORCE_TILE};
       int bl = best_lanes;
       for (int i = 0; i < 4 && rc == BDM_OK; ++i)
         if ((rc = trial(best, opts[i], &ms)) == BDM_OK && ms < best_ms) { best_ms = ms; bl = opts[i]; }

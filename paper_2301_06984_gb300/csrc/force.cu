@@ -230,8 +230,25 @@ __device__ __forceinline__ void flush_bbox(const DevBufs &B, const DevParams &P,
 // With static detection (use_static) only bricks with work left after
 // k_static are handed out: heavy ones whose need mask is not empty, then the
 // work list.
-__device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCounters *C, long long n_occ, int &phase,
-                                                      bool use_static) {
+// With brick_class 1 (the hybrid launch's dense part) light bricks (fewer than
+// light_max agents) are skipped; with brick_class 2 only light bricks are
+// handed out, from their own cursor.
+__device__ __forceinline__ long long next_force_brick(const DevBufs &B, const DevParams &P, DevCounters *C,
+                                                      long long n_occ, int &phase, bool use_static) {
+  if (P.brick_class == 2) {
+    while (true) {
+      const long long u = (long long)atomicAdd(&C->work_next2, 1ull);
+      long long o;
+      if (use_static) {
+        if (u >= (long long)C->work_n) return -1;
+        o = B.worklist[u];
+      } else {
+        if (u >= n_occ) return -1;
+        o = u;
+      }
+      if (B.brick_count[B.occ_list[o]] < P.light_max) return o;
+    }
+  }
   while (true) {
     if (phase < 2) {
       const unsigned long long u = atomicAdd(&C->heavy_take[phase], 1ull);
@@ -244,9 +261,17 @@ __device__ __forceinline__ long long next_force_brick(const DevBufs &B, DevCount
       continue;
     }
     const long long u = (long long)atomicAdd(&C->work_next, 1ull);
-    if (use_static) return u < (long long)C->work_n ? (long long)B.worklist[u] : -1;
-    if (u >= n_occ) return -1;
-    if (B.brick_count[B.occ_list[u]] < FORCE_HEAVY_LO) return u;  // heavy ones were listed
+    long long o;
+    if (use_static) {
+      if (u >= (long long)C->work_n) return -1;
+      o = B.worklist[u];
+    } else {
+      if (u >= n_occ) return -1;
+      o = u;
+      if (B.brick_count[B.occ_list[o]] >= FORCE_HEAVY_LO) continue;  // heavy ones were listed
+    }
+    if (P.brick_class == 1 && B.brick_count[B.occ_list[o]] < P.light_max) continue;
+    return o;
   }
 }
 
@@ -657,7 +682,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+      s_o = next_force_brick(B, P, C, n_occ, fetch_phase, use_static);
       s_next = 0;
     }
     __syncthreads();
@@ -1179,7 +1204,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
   while (true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-      s_o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+      s_o = next_force_brick(B, P, C, n_occ, fetch_phase, use_static);
       s_next = 0;
     }
     __syncthreads();
@@ -1528,7 +1553,7 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
   // so a warp on a brick with few agents to compute does not hold the others
   while (true) {
     long long o = 0;
-    if (lane == 0) o = next_force_brick(B, C, n_occ, fetch_phase, use_static);
+    if (lane == 0) o = next_force_brick(B, P, C, n_occ, fetch_phase, use_static);
     o = __shfl_sync(0xffffffffu, o, 0);
     if (o < 0) break;
     if (!BDM_IN(B.ctr, o < n_occ)) break;  // warp-uniform
@@ -1834,6 +1859,7 @@ __global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P
 
 __global__ void k_reset_work(DevBufs B) {
   B.ctr->work_next = 0;
+  B.ctr->work_next2 = 0;
   B.ctr->heavy_take[0] = B.ctr->heavy_take[1] = 0;
   B.ctr->fix_n = 0;
 }
@@ -2256,6 +2282,12 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
 #define LF(PR, MO, SP, TY) k_force<PR, MO, SP, TY><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
 #define LT(MO, TY) k_force_tile<MO, TY><<<g, TILE_WARPS * 32, 0, s>>>(B, P)
 #define LS(MO, TY) k_force_sparse<MO, TY><<<2 * g, SP_WARPS * 32, 0, s>>>(B, P)
+  // the hybrid launch: the lane-per-agent kernel (4 lanes) on the bricks that
+  // are not light, then the sparse kernel on the light ones
+  DevParams Pd = P, Pl = P;
+  Pd.brick_class = 1;
+  Pd.lanes_fixed = 4;
+  Pl.brick_class = 2;
   if (P.precision == 0) {
     switch (mode) {
       case FM_STEP: if (ty) LF(0, FM_STEP, false, true); else LF(0, FM_STEP, false, false); break;
@@ -2270,6 +2302,15 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
           if (ty) LT(FM_STEP, true); else LT(FM_STEP, false);
         } else if (P.lanes_fixed == FORCE_SPARSE) {
           if (ty) LS(FM_STEP, true); else LS(FM_STEP, false);
+        } else if (P.lanes_fixed == FORCE_HYBRID) {
+          if (ty) {
+            k_force<1, FM_STEP, false, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, Pd);
+            k_force_sparse<FM_STEP, true><<<2 * g, SP_WARPS * 32, 0, s>>>(B, Pl);
+          } else {
+            if (!P.walk && !P.grow && !P.die) k_force<1, FM_STEP, true, false><<<g, FORCE_WARPS * 32, 0, s>>>(B, Pd);
+            else k_force<1, FM_STEP, false, false><<<g, FORCE_WARPS * 32, 0, s>>>(B, Pd);
+            k_force_sparse<FM_STEP, false><<<2 * g, SP_WARPS * 32, 0, s>>>(B, Pl);
+          }
         } else if (ty) LF(1, FM_STEP, false, true);
         else if (!P.walk && !P.grow && !P.die) LF(1, FM_STEP, true, false);
         else LF(1, FM_STEP, false, false);
@@ -2279,6 +2320,14 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
           if (ty) LT(FM_FORCES, true); else LT(FM_FORCES, false);
         } else if (P.lanes_fixed == FORCE_SPARSE) {
           if (ty) LS(FM_FORCES, true); else LS(FM_FORCES, false);
+        } else if (P.lanes_fixed == FORCE_HYBRID) {
+          if (ty) {
+            k_force<1, FM_FORCES, false, true><<<g, FORCE_WARPS * 32, 0, s>>>(B, Pd);
+            k_force_sparse<FM_FORCES, true><<<2 * g, SP_WARPS * 32, 0, s>>>(B, Pl);
+          } else {
+            k_force<1, FM_FORCES, false, false><<<g, FORCE_WARPS * 32, 0, s>>>(B, Pd);
+            k_force_sparse<FM_FORCES, false><<<2 * g, SP_WARPS * 32, 0, s>>>(B, Pl);
+          }
         } else if (ty) LF(1, FM_FORCES, false, true);
         else LF(1, FM_FORCES, false, false);
         break;
@@ -2301,7 +2350,11 @@ void launch_force_fix(const DevBufs &B, const DevParams &P, const LaunchCfg &c, 
   if (mode == FM_FORCES) k_force_fix<FM_FORCES><<<2 * c.occ_blocks, FIXT_THREADS, 0, s>>>(B, P);
 }
 
-int force_launches(const DevParams &P) { (void)P; return 2; }
+// kernels of an iteration's force phase: k_reset_work, k_static (static
+// detection), the force kernel (two for the hybrid launch)
+int force_launches(const DevParams &P) {
+  return 2 + (P.detect_static ? 1 : 0) + ((P.precision == 1 && P.lanes_fixed == FORCE_HYBRID) ? 1 : 0);
+}
 int force_fix_launches(const DevParams &P) {
   return (P.precision == 1 && P.lanes_fixed != FORCE_TILE && P.lanes_fixed != FORCE_SPARSE) ? 1 : 0;
 }

@@ -109,6 +109,8 @@ DevParams make_dev_params(const bdm_params &P) {
   d.cband1 = (float)(4.0 * std::sqrt(3.0) * E);
   d.cband2 = (float)(10.0 * pow2i(-23));
   d.lanes_fixed = FORCE_LANES_DEFAULT;
+  d.brick_class = 0;
+  d.light_max = FORCE_LIGHT_MAX;
   d.kf = (float)P.k;
   d.gammaf = (float)P.gamma;
   d.dmaxf = (float)P.max_displacement;

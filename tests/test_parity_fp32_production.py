@@ -25,7 +25,7 @@ def _cuda():
     yield
 
 
-@pytest.mark.parametrize("lanes", [4, 0, -3])
+@pytest.mark.parametrize("lanes", [4, 0, -3, -4])
 def test_production_kernel_forces_blobs_100k_iterations_1_to_10(lanes):
     # no walk, no growth: the step instantiation that the 10M benchmark runs
     # (the lane-per-agent kernel's per-axis epilogue, 4 lanes per agent, the
@@ -39,7 +39,7 @@ def test_production_kernel_forces_blobs_100k_iterations_1_to_10(lanes):
         H.production_step_vs_oracle(s, P, what="blobs 100k iteration %d, kernel lanes=%d" % (it, lanes))
 
 
-@pytest.mark.parametrize("lanes", [4, 0, -3])
+@pytest.mark.parametrize("lanes", [4, 0, -3, -4])
 def test_production_kernel_forces_core_shell_with_walk(lanes):
     # random walk on the shell and the static skip: the shared step
     # instantiation with the one-lane epilogue, after the static pass, for
