@@ -521,22 +521,36 @@ __device__ __forceinline__ void write_compact(const DevBufs &B, const DevParams 
   if (P.n_types > 1) B.tp[k] = (uint8_t)((A.beh[i] >> BEH_TYPE_SHIFT) & 3u);
 }
 
-// Agent idx at sorted position kk of occupied brick o: its storage index, its
-// box-local compact record and, for the brick's first agent, the brick's
-// coordinates and simulation.
-__device__ __forceinline__ void place_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
-                                            long long o, uint32_t idx, long long kk, bool first) {
-  if (!BDM_IN(B.ctr, kk >= 0 && kk < B.ctr->n && idx < (uint32_t)B.cap && o < B.occ_cap)) return;
-  B.perm[kk] = idx;
+// The brick of agent idx (the same for every agent with the same brick
+// rank): its coordinates and simulation, from the agent's clamped box exactly
+// as k_keys formed the agent's key.
+__device__ __forceinline__ int4 brick_of_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
+                                               uint32_t idx) {
   const int s = (P.n_sims == 1) ? 0 : sim_of_agent(B.sim_off, P.n_sims, idx);
   const SimGeom &G = B.geom[s];
-  const double x = A.x[cur][idx], y = A.y[cur][idx], z = A.z[cur][idx];
   bool fb;
-  int bx = min(max(box_axis(x, G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
-  int by = min(max(box_axis(y, G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
-  int bz = min(max(box_axis(z, G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
-  write_compact(B, P, A, cur, G, idx, kk, bx, by, bz, x, y, z);
-  if (first) B.occ_info[o] = make_int4(bx >> 2, by >> 2, bz >> 2, s);
+  const int bx = min(max(box_axis(A.x[cur][idx], G.lo[0], G.lo_f[0], P, fb), 1), G.nb[0] - 2);
+  const int by = min(max(box_axis(A.y[cur][idx], G.lo[1], G.lo_f[1], P, fb), 1), G.nb[1] - 2);
+  const int bz = min(max(box_axis(A.z[cur][idx], G.lo[2], G.lo_f[2], P, fb), 1), G.nb[2] - 2);
+  return make_int4(bx >> 2, by >> 2, bz >> 2, s);
+}
+
+// Agent idx at sorted position kk of occupied brick o (br: the brick, from
+// brick_of_agent; lc: the agent's local box code): its storage index, its
+// box-local compact record and, for the brick's first agent, the brick's
+// coordinates and simulation.  The agent's box is the brick's corner box plus
+// its local box, so no box is computed per agent.
+__device__ __forceinline__ void place_agent(const DevBufs &B, const DevParams &P, const AgentSet &A, int cur,
+                                            long long o, uint32_t idx, unsigned lc, int4 br, long long kk, bool first) {
+  if (!BDM_IN(B.ctr, kk >= 0 && kk < B.ctr->n && idx < (uint32_t)B.cap && o < B.occ_cap && br.w >= 0 &&
+                         br.w < P.n_sims)) return;
+  B.perm[kk] = idx;
+  const SimGeom &G = B.geom[br.w];
+  int lx, ly, lz;
+  local_decode((int)lc, lx, ly, lz);
+  const double x = A.x[cur][idx], y = A.y[cur][idx], z = A.z[cur][idx];
+  write_compact(B, P, A, cur, G, idx, kk, 4 * br.x + lx, 4 * br.y + ly, 4 * br.z + lz, x, y, z);
+  if (first) B.occ_info[o] = br;
 }
 
 __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams P) {
@@ -546,6 +560,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
   __shared__ uint8_t s_gl[BS_SMEM_M];
   __shared__ unsigned s_cnt[64], s_off[64], s_cur[64];
   __shared__ int s_abort;
+  __shared__ int4 s_br;
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
@@ -564,7 +579,10 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
     }
     __syncthreads();
     if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
-    if (threadIdx.x == 0) s_abort = 0;
+    if (threadIdx.x == 0) {
+      s_abort = 0;
+      s_br = brick_of_agent(B, P, A, cur, B.bucket[S0]);
+    }
     __syncthreads();
     for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
       if (!BDM_IN(B.ctr, (long long)S0 + k < B.ctr->n)) break;
@@ -622,7 +640,7 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
       } else {
         for (unsigned q = 0; q < cnt; ++q) r += (B.arrival[S0 + lo + q] < idx);
       }
-      place_agent(B, P, A, cur, o, idx, (long long)S0 + lo + r, lo + r == 0);
+      place_agent(B, P, A, cur, o, idx, l, s_br, (long long)S0 + lo + r, lo + r == 0);
     }
     if (threadIdx.x < 64) {
       B.box_start[o * 64 + threadIdx.x] = S0 + s_off[threadIdx.x];
@@ -656,6 +674,12 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     }
     s_cnt[w][lane] = 0u;
     s_cnt[w][lane + 32] = 0u;
+    int4 br = make_int4(0, 0, 0, 0);
+    if (lane == 0) br = brick_of_agent(B, P, A, cur, B.bucket[S0]);
+    br.x = __shfl_sync(0xffffffffu, br.x, 0);
+    br.y = __shfl_sync(0xffffffffu, br.y, 0);
+    br.z = __shfl_sync(0xffffffffu, br.z, 0);
+    br.w = __shfl_sync(0xffffffffu, br.w, 0);
     __syncwarp();
     for (unsigned k = lane; k < m; k += 32) {
       const uint32_t idx = B.bucket[S0 + k];
@@ -694,7 +718,7 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
       const unsigned lo = s_off[w][l], cnt = s_cnt[w][l];
       unsigned r = 0;
       for (unsigned q = 0; q < cnt; ++q) r += (s_grp[w][lo + q] < idx);
-      place_agent(B, P, A, cur, o, idx, (long long)S0 + lo + r, lo + r == 0);
+      place_agent(B, P, A, cur, o, idx, l, br, (long long)S0 + lo + r, lo + r == 0);
     }
     B.box_start[o * 64 + lane] = S0 + s_off[w][lane];
     B.box_start[o * 64 + lane + 32] = S0 + s_off[w][lane + 32];
