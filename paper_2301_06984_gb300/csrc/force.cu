@@ -1766,7 +1766,7 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
 // (heavier ones stay on the heavy lists).  High occupancy hides the per-brick
 // latency that a force-kernel block would serialise.
 #define KS_WARPS 8
-__global__ void __launch_bounds__(KS_WARPS * 32) k_static(DevBufs B, DevParams P) {
+__global__ void __launch_bounds__(KS_WARPS * 32, 8) k_static(DevBufs B, DevParams P) {
   __shared__ unsigned long long s_dm[KS_WARPS][27];
   __shared__ unsigned s_bst[KS_WARPS][64], s_bcnt[KS_WARPS][64], s_work[KS_WARPS][64];
   DevCounters *C = B.ctr;
