@@ -1503,7 +1503,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
 // results in its queue order.  A lane whose queue is full evaluates the contact
 // itself.  No agent is listed for the fix-up pass.
 #define SP_WARPS 4
-#define SP_Q 8    // double-float contacts a lane queues per round
+#define SP_Q 4    // double-float contacts a lane queues per round
 template <int MODE, bool TYPES>
 __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, DevParams P) {
   static_assert(MODE == FM_STEP || MODE == FM_FORCES, "the sparse kernel computes forces");
@@ -1512,6 +1512,9 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
   __shared__ int s_nocc[SP_WARPS][27];
   __shared__ unsigned long long s_ndirty[SP_WARPS][27];
   __shared__ unsigned s_bst[SP_WARPS][65];
+  // and the first sorted position and agent count of each box of the 6 x 6 x 6
+  // region around the brick (local box coordinates -1..4)
+  __shared__ unsigned s_rst[SP_WARPS][216], s_rcnt[SP_WARPS][216];
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[SP_WARPS][6];
   __shared__ uint32_t s_dq[SP_WARPS][SP_Q][32];   // each lane's queued candidates (sorted positions)
@@ -1577,6 +1580,20 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
     if (lane == 0) s_bst[warp][64] = B.box_start[o * 64 + 63] + B.box_cnt[o * 64 + 63];
     const unsigned long long need = use_static ? B.need[o] : ~0ull;  // boxes with work
     __syncwarp();
+    for (int rb = lane; rb < 216; rb += 32) {
+      const int ax = rb % 6 - 1, ay = (rb / 6) % 6 - 1, az = rb / 36 - 1;
+      const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
+                     ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
+      const int occ = s_nocc[warp][bo];
+      unsigned st = 0, cnt = 0;
+      if (occ >= 0) {
+        const long long bx = (long long)occ * 64 + local_code(ax & 3, ay & 3, az & 3);
+        st = B.box_start[bx];
+        cnt = B.box_cnt[bx];
+      }
+      s_rst[warp][rb] = st;
+      s_rcnt[warp][rb] = cnt;
+    }
     // boxes with a clean stencil (no dirty box in it)
     unsigned long long clean = 0ull;
     if (use_static) {
@@ -1631,13 +1648,8 @@ __global__ void __launch_bounds__(SP_WARPS * 32, 8) k_force_sparse(DevBufs B, De
         int lx, ly, lz;
         local_decode(lb, lx, ly, lz);
         for (int sb = 0; sb < 27; ++sb) {
-          const int ax = lx + sb % 3 - 1, ay = ly + (sb / 3) % 3 - 1, az = lz + sb / 9 - 1;
-          const int bo = ((az < 0) ? 0 : (az > 3 ? 2 : 1)) * 9 + ((ay < 0) ? 0 : (ay > 3 ? 2 : 1)) * 3 +
-                         ((ax < 0) ? 0 : (ax > 3 ? 2 : 1));
-          const int occ = s_nocc[warp][bo];
-          if (occ < 0) continue;
-          const long long bx = (long long)occ * 64 + local_code(ax & 3, ay & 3, az & 3);
-          const unsigned st = B.box_start[bx], cnt = B.box_cnt[bx];
+          const int rb = (lx + sb % 3) + 6 * (ly + (sb / 3) % 3) + 36 * (lz + sb / 9);
+          const unsigned st = s_rst[warp][rb], cnt = s_rcnt[warp][rb];
           n_cand += cnt;
           const float4 of = s_off[sb];
           for (unsigned j = 0; j < cnt; ++j) {
