@@ -271,7 +271,7 @@ int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
  * tiled and sparse kernels evaluate every contact the FP32 error analysis does
  * not cover in double-float arithmetic in place, so they need no fix-up pass.
  * lanes = -4 (the default) selects the hybrid launch: the sparse kernel for the
- * bricks of fewer than 128 agents, the lane-per-agent kernel with 4 lanes for
+ * bricks of fewer than 192 agents, the lane-per-agent kernel with 4 lanes for
  * the others.  All give the same neighbour and contact decisions (FP64-exact)
  * and forces within the FP32-form tolerance; the choice takes effect at the
  * next iteration.  No effect on the FP64 form.  Errors: BDM_EINVAL (other lanes

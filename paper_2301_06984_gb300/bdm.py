@@ -311,7 +311,7 @@ class Simulation:
 
     def set_force_kernel(self, lanes=-4):
         """FP32 form: -4 = the hybrid launch (the default: the sparse kernel for
-        bricks of fewer than 128 agents, 4 lanes per agent for the others);
+        bricks of fewer than 192 agents, 4 lanes per agent for the others);
         1, 2, 4, 8, 16, 32 = the lane-per-agent kernel with that many lanes per
         agent; -1 = the same with the lanes chosen per box by its cost model;
         0 = the tiled kernel; -3 = the sparse kernel (the last two evaluate the

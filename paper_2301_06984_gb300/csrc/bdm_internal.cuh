@@ -379,12 +379,15 @@ struct LaunchCfg {
 #define FORCE_TILE 0
 #define FORCE_SPARSE (-3)
 #define FORCE_HYBRID (-4)  // the sparse kernel for light bricks, 4 lanes per agent for the others
-#define FORCE_LIGHT_MAX 128
+#define FORCE_LIGHT_MAX 192
 #define FORCE_LANES_DEFAULT FORCE_HYBRID
 
 // brick weight classes of the force kernels' largest-first order (agents)
 #define FORCE_HEAVY_HI 1024
 #define FORCE_HEAVY_LO 256
+// the hybrid launch's light bricks are never on the heavy lists (which the
+// lane-per-agent kernel takes whatever their class)
+static_assert(FORCE_LIGHT_MAX <= FORCE_HEAVY_LO, "light bricks must not be heavy-listed");
 
 
 #define SCAN_TILE 2048

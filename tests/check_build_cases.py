@@ -40,6 +40,19 @@ def case_blobs_fp32_production():
     _no_error(s, "blobs fp32")
 
 
+def case_blobs_fp32_every_kernel():
+    # the tiled, sparse and lane-per-agent kernels on their own (the default
+    # hybrid launch runs the last two together)
+    w = H.small_blobs(n=20_000, seed=7)
+    P = H.oracle_params(w)
+    for lanes in (0, -3, 4):
+        s = H.gpu_sim(w, precision="fp32", keep_forces=True)
+        s.set_force_kernel(lanes)
+        for it in range(2):
+            H.production_step_vs_oracle(s, P, what="check build blobs lanes=%d iteration %d" % (lanes, it + 1))
+        _no_error(s, "blobs fp32 lanes=%d" % lanes)
+
+
 def case_lattice_division_removal():
     w = W.lattice(m=8, steps=16)
     w.params["death_prob"] = 0.03
@@ -108,7 +121,8 @@ def case_grid_regrowth():
     _no_error(s, "grid regrowth")
 
 
-CASES = [case_uniform_fp64_sorted, case_blobs_fp32_production, case_lattice_division_removal,
+CASES = [case_uniform_fp64_sorted, case_blobs_fp32_production, case_blobs_fp32_every_kernel,
+         case_lattice_division_removal,
          case_core_shell_static_walk, case_ensemble, case_crowded_box_and_types, case_grid_regrowth]
 
 if __name__ == "__main__":

@@ -23,5 +23,5 @@ def test_check_build_runs_the_parity_cases_with_no_failed_check():
     r = subprocess.run([sys.executable, "-m", "tests.check_build_cases"], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=900)
     assert r.returncode == 0, r.stdout[-3000:] + r.stderr[-3000:]
-    assert r.stdout.count("ok case_") == 7
+    assert r.stdout.count("ok case_") == 8
     assert "libbdm_gb300_check.so" in r.stdout
