@@ -684,6 +684,8 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     br.z = __shfl_sync(0xffffffffu, br.z, 0);
     br.w = __shfl_sync(0xffffffffu, br.w, 0);
     __syncwarp();
+    // unrolled: several agents' loads in flight per lane
+#pragma unroll 4
     for (unsigned k = lane; k < m; k += 32) {
       const uint32_t idx = B.bucket[S0 + k];
       if (!BDM_IN(B.ctr, k < BSW_MAX && idx < (uint32_t)B.cap)) continue;
@@ -715,6 +717,7 @@ __global__ void __launch_bounds__(BSW_WARPS * 32) k_brick_sort_small(DevBufs B, 
     }
     __syncwarp();
     // stable rank inside the box = members with a smaller storage index
+#pragma unroll 2
     for (unsigned k = lane; k < m; k += 32) {
       const uint32_t idx = s_grp[w][k];
       const unsigned l = s_gl[w][k];
