@@ -54,12 +54,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--n", type=int, default=10_000_000, help="agents of the blob workload")
+    ap.add_argument("--n", type=int, default=10_000_000,
+                    help="agents of the blob workload (and of core_shell_leg)")
     ap.add_argument("--sample", type=int, default=0, help="agents of the oracle's CPU sample (0 = auto)")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="blobs", choices=["blobs", "ensemble", "core_shell", "lattice", "uniform"],
+    ap.add_argument("--workload", default="blobs",
+                    choices=["blobs", "ensemble", "core_shell", "core_shell_leg", "lattice", "uniform"],
                     help="blobs is the headline; the others measure the remaining configurations")
     ap.add_argument("--sort-every", type=int, default=10,
                     help="blobs: Morton re-sort cadence (0 = never; the headline workload uses 10)")
@@ -451,16 +453,16 @@ def leg_ensemble(args, steps=10, warmup=3):
             "batched_speedup": batched / per_sim, "clocks": clk.summary()}
 
 
-def leg_core_shell(args, steps=10, warmup=3):
-    """150M agents, 90% in a static core: agent-updates/s, the skipped
-    fraction, per-phase times and the algorithmic HBM throughput of the
-    iteration."""
+def leg_core_shell(args, steps=10, warmup=3, n=150_000_000):
+    """n agents (150M by default), 90% in a static core: agent-updates/s, the
+    skipped fraction, per-phase times and the algorithmic HBM throughput of
+    the iteration."""
     import torch
 
     from paper_2301_06984_gb300 import bdm
     from paper_2301_06984_gb300 import workloads as W
     stream = torch.cuda.current_stream()
-    w = W.core_shell()
+    w = W.core_shell(n=n)
     st = CORE_SHELL_SETTINGS
     sim = bdm.Simulation.from_workload(w, box_edge=st["box_edge"], sort_every=st["sort_every"])
     sim.set_force_kernel(st["lanes"])
@@ -478,8 +480,8 @@ def leg_core_shell(args, steps=10, warmup=3):
     bytes_step = STEP_BYTES_MOVING * (w.n - stat) + STEP_BYTES_STATIC * stat
     peaks = measured_peaks()
     gbs = bytes_step / (ms / steps * 1e-3) / 1e9
-    return {"workload": "core_shell-150M: FCC static core (90%%) + random-walk shell (10%%), d = 10 um, R = 10 um, "
-                        "static-agent skip on, FP32 form (%d agents)" % w.n, "settings": st, "steps": steps,
+    return {"workload": "core_shell-%d: FCC static core (90%%) + random-walk shell (10%%), d = 10 um, R = 10 um, "
+                        "static-agent skip on, FP32 form" % w.n, "settings": st, "steps": steps,
             "warmup": warmup, "value": w.n * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
             "skipped_fraction": stat / w.n,
             "hbm": {"bytes_per_step_algorithmic": bytes_step, "achieved_gbs": gbs, "peak_gbs": peaks["hbm_gbs"],
@@ -498,6 +500,13 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "core_shell_leg":
+        # the default line's core + shell leg on its own, at --n agents (for
+        # profiling a smaller case of the same workload)
+        import torch
+        torch.cuda.set_device(local)
+        print(json.dumps(leg_core_shell(args, steps=args.steps, warmup=max(3, args.warmup), n=args.n)), flush=True)
+        return 0
     if args.workload != "blobs":
         return run_other(args)
 
