@@ -775,9 +775,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
           if (cost < best) { best = cost; S = 1 << ls; }
         }
       }
-      const int sub = lane & (S - 1);
-      const unsigned G_ = 32u / S;
-      for (unsigned q0 = 0; q0 < nq; q0 += G_) {
+      // With 4 lanes per agent the lanes follow the agents still to do: 2
+      // lanes (16 agents a pass) while 11 or more are left, so that a crowded
+      // box stages its stencil fewer times, and a last pass of 4 agents or
+      // fewer spread over the whole warp (8, 16 or 32 lanes per agent).
+      const int S0 = S;
+      for (unsigned q0 = 0; q0 < nq; q0 += 32u / (unsigned)S) {
+        if (PREC == 1 && S0 == 4) {
+          const unsigned rem = nq - q0;
+          S = (rem >= 11u) ? 2 : (rem <= 1u) ? 32 : (rem <= 2u) ? 16 : (rem <= 4u) ? 8 : 4;
+        }
+        const int sub = lane & (S - 1);
         const unsigned qi = q0 + (unsigned)(lane / S);
         bool valid = qi < nq;
         unsigned kq = qbase + (valid ? qi : 0u);
