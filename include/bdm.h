@@ -261,7 +261,8 @@ int bdm_autotune(bdm_sim *sim, int trial_steps, int what, bdm_tuning *out);
  * lane-per-agent kernel: a warp takes a box's agents, that many lanes split
  * each agent's candidates, and each lane queues its prefiltered pairs before
  * evaluating them (with 4, the lanes follow the agents still to do in the
- * box: 2 while 11 or more are left, 8 to 32 for a last pass of 4 or fewer);
+ * box: 2 while 11 or more are left, 8 to 32 for a last pass of 4 or
+ * fewer);
  * agents whose FP32 error bound is not small against their
  * tolerance are finished by a fix-up pass.  lanes = -1 selects the same kernel
  * with the lanes chosen per box by a cost model.  lanes = 0 selects the tiled

@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
   __shared__ float4 s_c[FORCE_WARPS][CHUNK];
   __shared__ uint32_t s_kj[FORCE_WARPS][CHUNK];
   __shared__ uint8_t s_q[FORCE_WARPS][CHUNK][32];
-  __shared__ unsigned s_pre[FORCE_WARPS][28], s_st[FORCE_WARPS][28];
+  __shared__ unsigned s_pre[FORCE_WARPS][32], s_kb[FORCE_WARPS][32];
   // several agent types: the staged candidates' types and the pair constants
   __shared__ uint8_t s_tp[FORCE_WARPS][CHUNK];
   __shared__ float s_tkf[16], s_tgf[16];
@@ -760,8 +760,11 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
         if (lane >= of) pre += y;
       }
       const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
-      if (lane <= 27) s_pre[warp][lane] = pre - nb_cnt;  // s_pre[27] = ctot
-      if (lane < 27) s_st[warp][lane] = nb_st;
+      // box starts in the stencil (s_pre[27] = ctot, then UINT_MAX: the
+      // staging's search needs no range test) and each box's first sorted
+      // position minus its start
+      s_pre[warp][lane] = (lane <= 27) ? pre - nb_cnt : 0xFFFFFFFFu;
+      s_kb[warp][lane] = nb_st - (pre - nb_cnt);
       __syncwarp();
       // lanes per agent: split the candidates of small boxes over several lanes
       int S = 1;
@@ -778,7 +781,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
       // With 4 lanes per agent the lanes follow the agents still to do: 2
       // lanes (16 agents a pass) while 11 or more are left, so that a crowded
       // box stages its stencil fewer times, and a last pass of 4 agents or
-      // fewer spread over the whole warp (8, 16 or 32 lanes per agent).
+      // fewer spread over the whole warp (8, 16 or 32 lanes per agent).  One
+      // lane per agent would stage less again, but its single FP32 sum over a
+      // crowded stencil loses accuracy.
       const int S0 = S;
       for (unsigned q0 = 0; q0 < nq; q0 += 32u / (unsigned)S) {
         if (PREC == 1 && S0 == 4) {
@@ -846,9 +851,9 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 int lo = 0;
 #pragma unroll
                 for (int step = 16; step > 0; step >>= 1)
-                  if (lo + step <= 26 && s_pre[warp][lo + step] <= p) lo += step;
+                  if (s_pre[warp][lo + step] <= p) lo += step;
                 boxs[m] = lo;
-                kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
+                kjs[m] = s_kb[warp][lo] + p;
                 if (!BDM_IN(B.ctr, p >= ctot || (long long)kjs[m] < C->n)) kjs[m] = 0;
               }
               float4 cs[PER_LANE];
@@ -1168,7 +1173,7 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
   __shared__ unsigned s_ctr[TILE_WARPS][4];  // candidates, neighbours, contacts, exact pairs
   __shared__ float4 s_off[27];
   __shared__ unsigned long long s_bb[TILE_WARPS][6];
-  __shared__ unsigned s_pre[TILE_WARPS][28], s_st[TILE_WARPS][28];
+  __shared__ unsigned s_pre[TILE_WARPS][32], s_kb[TILE_WARPS][32];
   __shared__ float4 s_own[TILE_WARPS][32];          // the group's agents' FP32 records
   __shared__ uint8_t s_otp[TILE_WARPS][32];         // TYPES: their types
   __shared__ float4 s_c[TILE_WARPS][TCH];           // the staged chunk (offset applied)
@@ -1287,8 +1292,11 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
         if (lane >= of) pre += y;
       }
       const unsigned ctot = __shfl_sync(0xffffffffu, pre, 31);
-      if (lane <= 27) s_pre[warp][lane] = pre - nb_cnt;  // s_pre[27] = ctot
-      if (lane < 27) s_st[warp][lane] = nb_st;
+      // box starts in the stencil (s_pre[27] = ctot, then UINT_MAX: the
+      // staging's search needs no range test) and each box's first sorted
+      // position minus its start
+      s_pre[warp][lane] = (lane <= 27) ? pre - nb_cnt : 0xFFFFFFFFu;
+      s_kb[warp][lane] = nb_st - (pre - nb_cnt);
       __syncwarp();
       for (unsigned q0 = 0; q0 < nq; q0 += 32) {
         const unsigned qi = q0 + (unsigned)lane;
@@ -1324,9 +1332,9 @@ __global__ void __launch_bounds__(TILE_WARPS * 32, 4) k_force_tile(DevBufs B, De
               int lo = 0;
 #pragma unroll
               for (int st = 16; st > 0; st >>= 1)
-                if (lo + st <= 26 && s_pre[warp][lo + st] <= p) lo += st;
+                if (s_pre[warp][lo + st] <= p) lo += st;
               boxs[m] = lo;
-              kjs[m] = s_st[warp][lo] + (p - s_pre[warp][lo]);
+              kjs[m] = s_kb[warp][lo] + p;
               if (!BDM_IN(B.ctr, p >= ctot || (long long)kjs[m] < C->n)) kjs[m] = 0;
             }
             float4 cs[2];
@@ -1888,17 +1896,21 @@ __global__ void k_reset_work(DevBufs B) {
 // The FP32-form agents that the lane-per-agent force kernel listed (an FP32
 // error bound not small against the agent's tolerance, or a summed pair-force
 // magnitude so small that the absolute floor dominates) are evaluated again
-// here, one thread per listed agent: each thread walks its agent's 27-box
-// stencil in the canonical order, with k_force's FP32
-// prefilter and decisions (FP64 inside the error bands); every contact the
-// FP32 error analysis does not cover (|F| < low_scale, delta < graze, d^2 <
-// close2) in double-float (contact_df), the others with the force kernel's
-// FP32 arithmetic; the contributions summed in FP64, rounded to FP32 once.
-// The listed agents are few (1-2% of a dense tissue), so each warp's lanes
-// are independent agents and no warp work is spent on an agent's stencil set-up.
+// here, FIX_LANES lanes per listed agent: each lane walks every FIX_LANES-th
+// box of the agent's 27-box stencil, with k_force's FP32 prefilter and
+// decisions (FP64 inside the error bands); every contact the FP32 error
+// analysis does not cover (|F| < low_scale, delta < graze, d^2 < close2) in
+// double-float (contact_df), the others with the force kernel's FP32
+// arithmetic; the contributions summed in FP64 (per lane, then over the
+// agent's lanes in a fixed tree), rounded to FP32 once.  The listed agents are
+// few (1-2% of a dense tissue), so the pass takes a few waves, and its time
+// is a warp's latency: 16 lanes per agent split that walk, and the FP64 and
+// double-float pairs of a warp's 2 agents, where a lane per agent would
+// serialise those of 32.
 #define FIXT_THREADS 128
+#define FIX_LANES 16
 template <int MODE>
-__global__ void __launch_bounds__(FIXT_THREADS, 6) k_force_fix(DevBufs B, DevParams P) {
+__global__ void __launch_bounds__(FIXT_THREADS, 8) k_force_fix(DevBufs B, DevParams P) {
   __shared__ float s_tkf[16], s_tgf[16];
   __shared__ double s_tkd[16], s_tgd[16];
   __shared__ DF s_tk2[16], s_tg2[16];
@@ -1924,11 +1936,15 @@ __global__ void __launch_bounds__(FIXT_THREADS, 6) k_force_fix(DevBufs B, DevPar
   const long long step = C->step;
   unsigned c_static = 0, c_moved = 0, n_exact = 0;
   int wsim = -1;
-  // warp-uniform trip count (the bounding-box flushes are warp-wide)
-  const unsigned long long stride = (unsigned long long)gridDim.x * FIXT_THREADS;
-  for (unsigned long long e0 = (unsigned long long)blockIdx.x * FIXT_THREADS + (threadIdx.x & ~31u); e0 < nfix;
-       e0 += stride) {
-    const unsigned long long e = e0 + (unsigned long long)lane;
+  // FIX_LANES lanes per listed agent, each walking every FIX_LANES-th box of
+  // its stencil; warp-uniform trip count (the bounding-box flushes and the
+  // lanes' sums are warp-wide)
+  const int sub = lane & (FIX_LANES - 1);
+  const unsigned long long stride = (unsigned long long)gridDim.x * (FIXT_THREADS / FIX_LANES);
+  for (unsigned long long e0 = (unsigned long long)blockIdx.x * (FIXT_THREADS / FIX_LANES) +
+                               (threadIdx.x & ~31u) / FIX_LANES;
+       e0 < nfix; e0 += stride) {
+    const unsigned long long e = e0 + (unsigned long long)(lane / FIX_LANES);
     bool valid = e < nfix && BDM_IN(B.ctr, (long long)e < B.cap);
     const uint4 ent = valid ? B.fix[e] : make_uint4(0u, 0u, 0u, 0u);
     const unsigned kq = ent.x;
@@ -1949,14 +1965,14 @@ __global__ void __launch_bounds__(FIXT_THREADS, 6) k_force_fix(DevBufs B, DevPar
       }
     }
     double hx = 0.0, hy = 0.0, hz = 0.0;
+    const SimGeom &G = B.geom[info.w];
     if (valid) {
-      const SimGeom &G = B.geom[info.w];
       const float4 cq = B.c32[kq];
       const dbl4 dq = exact_of<1>(B, A, cur, kq);
       const int tq4 = (P.n_types > 1) ? 4 * (int)B.tp[kq] : 0;
       int lx, ly, lz;
       local_decode(lb, lx, ly, lz);
-      for (int sb = 0; sb < 27; ++sb) {
+      for (int sb = sub; sb < 27; sb += FIX_LANES) {
         const int ax = lx + sb % 3 - 1, ay = ly + (sb / 3) % 3 - 1, az = lz + sb / 9 - 1;
         const int X = info.x + ((ax < 0) ? -1 : (ax > 3 ? 1 : 0));
         const int Y = info.y + ((ay < 0) ? -1 : (ay > 3 ? 1 : 0));
@@ -1999,6 +2015,13 @@ __global__ void __launch_bounds__(FIXT_THREADS, 6) k_force_fix(DevBufs B, DevPar
           }
         }
       }
+    }
+    for (int of = FIX_LANES >> 1; of > 0; of >>= 1) {
+      hx += __shfl_xor_sync(0xffffffffu, hx, of);
+      hy += __shfl_xor_sync(0xffffffffu, hy, of);
+      hz += __shfl_xor_sync(0xffffffffu, hz, of);
+    }
+    if (valid && sub == 0) {
       const uint32_t iq = B.perm[kq];
       double px = 0.0, py = 0.0, pz = 0.0;
       if (MODE == FM_STEP) { px = A.x[cur][iq]; py = A.y[cur][iq]; pz = A.z[cur][iq]; }

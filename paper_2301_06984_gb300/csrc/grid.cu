@@ -564,90 +564,110 @@ __global__ void __launch_bounds__(BS_THREADS) k_brick_sort(DevBufs B, DevParams 
   __shared__ unsigned s_cnt[64], s_off[64], s_cur[64];
   __shared__ int s_abort;
   __shared__ int4 s_br;
+  __shared__ long long s_list[BS_THREADS];
+  __shared__ int s_nlist;
   DevCounters *C = B.ctr;
   if (C->error) return;
   const AgentSet A = *B.A;
   const int cur = (int)(C->step & 1);
   const long long n_occ = C->n_occ;
-  for (long long o = blockIdx.x; o < n_occ; o += gridDim.x) {
-    const int g = B.occ_list[o];
-    const unsigned S0 = B.brick_start[g];
-    const unsigned m = B.brick_count[g];
-    if (m <= BSW_MAX) continue;  // block-uniform: k_brick_sort_small's brick
-    const bool onchip = m <= BS_SMEM_M;
-    if (threadIdx.x == 0 && m >= FORCE_HEAVY_LO) {
-      // heavy bricks, listed for the force kernels' largest-first order
-      if (m >= FORCE_HEAVY_HI) B.heavy[atomicAdd(&C->heavy_n[0], 1ull)] = (int32_t)o;
-      else B.heavy[B.occ_cap - 1 - (long long)atomicAdd(&C->heavy_n[1], 1ull)] = (int32_t)o;
+  // The block's bricks are o = blockIdx.x + i gridDim.x.  Its threads test
+  // BS_THREADS of them at a time and list those above BSW_MAX agents (the
+  // others are k_brick_sort_small's), so that the block does not walk the
+  // many light bricks one dependent load pair at a time.  The bricks are
+  // independent: the order in which a block sorts them changes no result.
+  for (long long r0 = 0; (long long)blockIdx.x + (long long)gridDim.x * r0 < n_occ; r0 += BS_THREADS) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_nlist = 0;
+    __syncthreads();
+    {
+      const long long ot = (long long)blockIdx.x + (long long)gridDim.x * (r0 + threadIdx.x);
+      if (ot < n_occ && B.brick_count[B.occ_list[ot]] > BSW_MAX) s_list[atomicAdd(&s_nlist, 1)] = ot;
     }
     __syncthreads();
-    if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
-    if (threadIdx.x == 0) {
-      s_abort = 0;
-      s_br = brick_of_agent(B, P, A, cur, B.bucket[S0]);
-    }
-    __syncthreads();
-    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-      if (!BDM_IN(B.ctr, (long long)S0 + k < B.ctr->n)) break;
-      const uint32_t idx = B.bucket[S0 + k];
-      if (!BDM_IN(B.ctr, idx < (uint32_t)B.cap)) continue;
-      const unsigned l = B.key[idx] & 63u;
-      if (onchip) { s_idx[k] = idx; s_l[k] = (uint8_t)l; }
-      atomicAdd(&s_cnt[l], 1u);
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      const int lane = threadIdx.x;
-      unsigned a = s_cnt[lane], b = s_cnt[lane + 32];
-      unsigned xa = a, xb = b;
-      for (int d = 1; d < 32; d <<= 1) {
-        unsigned ya = __shfl_up_sync(0xffffffffu, xa, d), yb = __shfl_up_sync(0xffffffffu, xb, d);
-        if (lane >= d) { xa += ya; xb += yb; }
+    const int nl = s_nlist;
+    for (int li = 0; li < nl; ++li) {
+      const long long o = s_list[li];
+      const int g = B.occ_list[o];
+      const unsigned S0 = B.brick_start[g];
+      const unsigned m = B.brick_count[g];
+      const bool onchip = m <= BS_SMEM_M;
+      if (threadIdx.x == 0 && m >= FORCE_HEAVY_LO) {
+        // heavy bricks, listed for the force kernels' largest-first order
+        if (m >= FORCE_HEAVY_HI) B.heavy[atomicAdd(&C->heavy_n[0], 1ull)] = (int32_t)o;
+        else B.heavy[B.occ_cap - 1 - (long long)atomicAdd(&C->heavy_n[1], 1ull)] = (int32_t)o;
       }
-      unsigned ta = __shfl_sync(0xffffffffu, xa, 31);
-      s_off[lane] = xa - a;
-      s_off[lane + 32] = ta + xb - b;
-      s_cur[lane] = xa - a;
-      s_cur[lane + 32] = ta + xb - b;
-      unsigned mx = max(a, b);
-      for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, d));
-      if (lane == 0 && mx > BDM_MAX_BOX_AGENTS) {
-        atomicCAS(&C->error, 0, (int)DEV_EBOX);
-        s_abort = 1;
+      __syncthreads();
+      if (threadIdx.x < 64) s_cnt[threadIdx.x] = 0;
+      if (threadIdx.x == 0) {
+        s_abort = 0;
+        s_br = brick_of_agent(B, P, A, cur, B.bucket[S0]);
       }
-    }
-    __syncthreads();
-    if (s_abort) return;  // block-uniform
-    // group by box (arrival order inside a group)
-    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-      uint32_t idx;
-      unsigned l;
-      if (onchip) { idx = s_idx[k]; l = s_l[k]; }
-      else { idx = B.bucket[S0 + k]; l = B.key[idx] & 63u; }
-      const unsigned pos = atomicAdd(&s_cur[l], 1u);
-      if (!BDM_IN(B.ctr, pos < m && (!onchip || pos < BS_SMEM_M))) continue;
-      if (onchip) { s_grp[pos] = idx; s_gl[pos] = (uint8_t)l; }
-      else B.arrival[S0 + pos] = idx;
-    }
-    __syncthreads();
-    // stable rank inside the box = members with a smaller storage index
-    for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
-      uint32_t idx;
-      unsigned l;
-      if (onchip) { idx = s_grp[k]; l = s_gl[k]; }
-      else { idx = B.arrival[S0 + k]; l = B.key[idx] & 63u; }
-      const unsigned lo = s_off[l], cnt = s_cnt[l];
-      unsigned r = 0;
-      if (onchip) {
-        for (unsigned q = 0; q < cnt; ++q) r += (s_grp[lo + q] < idx);
-      } else {
-        for (unsigned q = 0; q < cnt; ++q) r += (B.arrival[S0 + lo + q] < idx);
+      __syncthreads();
+#pragma unroll 4
+      for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+        if (!BDM_IN(B.ctr, (long long)S0 + k < B.ctr->n)) break;
+        const uint32_t idx = B.bucket[S0 + k];
+        if (!BDM_IN(B.ctr, idx < (uint32_t)B.cap)) continue;
+        const unsigned l = B.key[idx] & 63u;
+        if (onchip) { s_idx[k] = idx; s_l[k] = (uint8_t)l; }
+        atomicAdd(&s_cnt[l], 1u);
       }
-      place_agent(B, P, A, cur, o, idx, l, s_br, (long long)S0 + lo + r, lo + r == 0);
-    }
-    if (threadIdx.x < 64) {
-      B.box_start[o * 64 + threadIdx.x] = S0 + s_off[threadIdx.x];
-      B.box_cnt[o * 64 + threadIdx.x] = s_cnt[threadIdx.x];
+      __syncthreads();
+      if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        unsigned a = s_cnt[lane], b = s_cnt[lane + 32];
+        unsigned xa = a, xb = b;
+        for (int d = 1; d < 32; d <<= 1) {
+          unsigned ya = __shfl_up_sync(0xffffffffu, xa, d), yb = __shfl_up_sync(0xffffffffu, xb, d);
+          if (lane >= d) { xa += ya; xb += yb; }
+        }
+        unsigned ta = __shfl_sync(0xffffffffu, xa, 31);
+        s_off[lane] = xa - a;
+        s_off[lane + 32] = ta + xb - b;
+        s_cur[lane] = xa - a;
+        s_cur[lane + 32] = ta + xb - b;
+        unsigned mx = max(a, b);
+        for (int d = 16; d > 0; d >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, d));
+        if (lane == 0 && mx > BDM_MAX_BOX_AGENTS) {
+          atomicCAS(&C->error, 0, (int)DEV_EBOX);
+          s_abort = 1;
+        }
+      }
+      __syncthreads();
+      if (s_abort) return;  // block-uniform
+      // group by box (arrival order inside a group)
+      for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+        uint32_t idx;
+        unsigned l;
+        if (onchip) { idx = s_idx[k]; l = s_l[k]; }
+        else { idx = B.bucket[S0 + k]; l = B.key[idx] & 63u; }
+        const unsigned pos = atomicAdd(&s_cur[l], 1u);
+        if (!BDM_IN(B.ctr, pos < m && (!onchip || pos < BS_SMEM_M))) continue;
+        if (onchip) { s_grp[pos] = idx; s_gl[pos] = (uint8_t)l; }
+        else B.arrival[S0 + pos] = idx;
+      }
+      __syncthreads();
+      // stable rank inside the box = members with a smaller storage index
+#pragma unroll 2
+      for (unsigned k = threadIdx.x; k < m; k += blockDim.x) {
+        uint32_t idx;
+        unsigned l;
+        if (onchip) { idx = s_grp[k]; l = s_gl[k]; }
+        else { idx = B.arrival[S0 + k]; l = B.key[idx] & 63u; }
+        const unsigned lo = s_off[l], cnt = s_cnt[l];
+        unsigned r = 0;
+        if (onchip) {
+          for (unsigned q = 0; q < cnt; ++q) r += (s_grp[lo + q] < idx);
+        } else {
+          for (unsigned q = 0; q < cnt; ++q) r += (B.arrival[S0 + lo + q] < idx);
+        }
+        place_agent(B, P, A, cur, o, idx, l, s_br, (long long)S0 + lo + r, lo + r == 0);
+      }
+      if (threadIdx.x < 64) {
+        B.box_start[o * 64 + threadIdx.x] = S0 + s_off[threadIdx.x];
+        B.box_cnt[o * 64 + threadIdx.x] = s_cnt[threadIdx.x];
+      }
     }
   }
 }
