@@ -948,8 +948,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
               for (unsigned m = 0; m < mx; ++m) {
                 if (m >= qlen) continue;
                 const unsigned i = s_q[warp][m][lane];
-                const unsigned kj = skj[i];
-                if (kj == kq) continue;  // the agent itself
+                const unsigned kj = (PREC == 0) ? skj[i] : 0u;
+                if (PREC == 0 && kj == kq) continue;  // the agent itself
                 if (PREC == 0) {
                   const dbl4 cj = B.c64[kj];
                   if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
@@ -969,15 +969,17 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                 const float4 c = sc[i];
                 const float ex = __fsub_rn(cq.x, c.x), ey = __fsub_rn(cq.y, c.y), ez = __fsub_rn(cq.z, c.z);
                 const float d2 = fmaf(ex, ex, fmaf(ey, ey, __fmul_rn(ez, ez)));
+                // the agent itself: its own staged record, at d2 = 0 exactly
+                if (d2 < TINY2 && skj[i] == kq) continue;
                 const bool band = (d2 > P.R2_lo_f) || (d2 < TINY2);
                 if (MODE == FM_COUNT_NBR || MODE == FM_LIST_NBR) {
                   bool isn = true;
                   if (band && d2 > P.R2_lo_f) {
                     atomicAdd(&s_ctr[warp][3], 1u);
-                    isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj));
+                    isn = is_nbr_f64(P, exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, skj[i]));
                   }
                   if (isn) {
-                    if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[kj];
+                    if (MODE == FM_LIST_NBR) B.nbr_out[lbase + nnb] = (long long)B.perm[skj[i]];
                     nnb++;
                   }
                   continue;
@@ -1001,8 +1003,8 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   if (k.delta < P.graze_exact || d2 < P.close2) {
                     atomicAdd(&s_ctr[warp][3], 1u);
                     float tx, ty, tz;
-                    fscale += contact_int(exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), P.fix_shift, kf,
-                                          gf, tx, ty, tz);
+                    fscale += contact_int(exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, skj[i]), P.fix_shift,
+                                          kf, gf, tx, ty, tz);
                     ffx += tx; ffy += ty; ffz += tz;
                     nnb++;
                     ncont++;
@@ -1013,7 +1015,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
                   atomicAdd(&s_ctr[warp][3], 1u);
                   double gx = 0.0, gy = 0.0, gz = 0.0;
                   const int r = pair_f64_k(P.R2, TYPES ? s_tkd[ab] : P.k, TYPES ? s_tgd[ab] : P.gamma,
-                                           exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, kj), gx, gy, gz);
+                                           exact_of<1>(B, A, cur, kq), exact_of<1>(B, A, cur, skj[i]), gx, gy, gz);
                   nnb += (r > 0);
                   if (r == 2) {
                     ncont++;
