@@ -414,8 +414,8 @@ void launch_debug_boxes(const DevBufs &B, const DevParams &P, const LaunchCfg &c
                         long long *out_rank, cudaStream_t s);
 void launch_diam_to_f64(const DevBufs &B, const DevParams &P, const LaunchCfg &c, double *out, cudaStream_t s);
 void launch_init_agents(const DevBufs &B, const DevParams &P, const LaunchCfg &c, const double *diam_in,
-                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n,
+                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n, int *bad,
                         cudaStream_t s);
-void launch_validate(const double *x, const double *y, const double *z, const double *d, long long n,
-                     int *bad, cudaStream_t s);
+void launch_positions_in(const double *x, const double *y, const double *z, const AgentSet &A, long long n, int *bad,
+                         const LaunchCfg &c, cudaStream_t s);
 void launch_nbr_offsets(const DevBufs &B, const DevParams &P, cudaStream_t s);

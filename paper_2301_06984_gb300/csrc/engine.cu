@@ -32,6 +32,10 @@ struct bdm_sim {
   cudaStream_t user = nullptr;
   cudaStream_t own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // bdm_set_agents: a second stream that copies and checks the positions
+  // while the other input arrays are still crossing the host link
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   std::string err = "no error";
   long long cap = 0;
   int n_sims = 1;
@@ -457,8 +461,11 @@ int bdm_create(const bdm_params *params, void *stream, bdm_sim **out) {
     return bail(BDM_ECUDA);
   }
   if (cudaStreamCreateWithFlags(&s->own, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->aux, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_in, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_a, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_b, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost((void **)&s->h_ctr, sizeof(DevCounters)) != cudaSuccess) {
     cudaGetLastError();
     s->err = "stream/event/pinned allocation failed";
@@ -505,6 +512,9 @@ void bdm_destroy(bdm_sim *s) {
   if (s->h_ctr) cudaFreeHost(s->h_ctr);
   if (s->ev_in) cudaEventDestroy(s->ev_in);
   if (s->ev_out) cudaEventDestroy(s->ev_out);
+  if (s->ev_a) cudaEventDestroy(s->ev_a);
+  if (s->ev_b) cudaEventDestroy(s->ev_b);
+  if (s->aux) cudaStreamDestroy(s->aux);
   if (s->own) cudaStreamDestroy(s->own);
   delete s;
 }
@@ -548,14 +558,24 @@ int bdm_set_agents(bdm_sim *s, int64_t n, const double *xyz, const double *diam,
   const AgentSet &A = s->sets[0];
   const AgentSet &T = s->sets[1];  // staging
   if (n > 0) {
-    // P_t into both position buffers (no movement history yet): one copy
-    // from the caller, the second buffer filled on the device
-    CK(cudaMemcpyAsync(A.x[0], xyz, sizeof(double) * n, kind, s->own));
-    CK(cudaMemcpyAsync(A.y[0], xyz + n, sizeof(double) * n, kind, s->own));
-    CK(cudaMemcpyAsync(A.z[0], xyz + 2 * n, sizeof(double) * n, kind, s->own));
-    CK(cudaMemcpyAsync(A.x[1], A.x[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
-    CK(cudaMemcpyAsync(A.y[1], A.y[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
-    CK(cudaMemcpyAsync(A.z[1], A.z[0], sizeof(double) * n, cudaMemcpyDeviceToDevice, s->own));
+    // P_t into both position buffers (no movement history yet), checked on
+    // the way (finite positions within +-1e9 um, then finite positive
+    // diameters in the init kernel); a failure leaves no agents set.  From
+    // host memory the positions cross the link first, and their second copy
+    // and check run on the auxiliary stream while the diameters cross.
+    int *bad = (int *)s->B.scan_b;  // scratch
+    CK(cudaMemsetAsync(bad, 0, sizeof(int), s->own));
+    if (mem == BDM_HOST) {
+      CK(cudaMemcpyAsync(A.x[0], xyz, sizeof(double) * n, kind, s->own));
+      CK(cudaMemcpyAsync(A.y[0], xyz + n, sizeof(double) * n, kind, s->own));
+      CK(cudaMemcpyAsync(A.z[0], xyz + 2 * n, sizeof(double) * n, kind, s->own));
+      CK(cudaEventRecord(s->ev_a, s->own));
+      CK(cudaStreamWaitEvent(s->aux, s->ev_a, 0));
+      launch_positions_in(A.x[0], A.y[0], A.z[0], A, n, bad, s->lc, s->aux);
+      CK(cudaEventRecord(s->ev_b, s->aux));
+    } else {
+      launch_positions_in(xyz, xyz + n, xyz + 2 * n, A, n, bad, s->lc, s->own);
+    }
     const double *d_diam = diam;
     const double *d_vol = nullptr;
     const uint64_t *d_uid = nullptr;
@@ -571,16 +591,12 @@ int bdm_set_agents(bdm_sim *s, int64_t n, const double *xyz, const double *diam,
       d_uid = uid;
       d_beh = behavior;
     }
-    launch_init_agents(s->B, s->dp, s->lc, d_diam, d_vol, d_uid, d_beh, n, s->own);
-    // validation on the device copies (finite positions within +-1e9 um,
-    // finite positive diameters); a failure leaves no agents set
-    int *bad = (int *)s->B.scan_b;  // scratch
-    CK(cudaMemsetAsync(bad, 0, sizeof(int), s->own));
-    launch_validate(A.x[0], A.y[0], A.z[0], d_diam, n, bad, s->own);
+    launch_init_agents(s->B, s->dp, s->lc, d_diam, d_vol, d_uid, d_beh, n, bad, s->own);
+    if (mem == BDM_HOST) CK(cudaStreamWaitEvent(s->own, s->ev_b, 0));
     int hb = 0;
     CK(cudaMemcpyAsync(&hb, bad, sizeof(int), cudaMemcpyDeviceToHost, s->own));
     CK(cudaStreamSynchronize(s->own));
-    s->kernels += 3;
+    s->kernels += 2;
     if (hb) {
       s->have_agents = false;
       return fail(s, BDM_EINVAL, "non-finite or out-of-range position or diameter (no agents are set)");

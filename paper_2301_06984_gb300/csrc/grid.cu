@@ -878,12 +878,15 @@ __global__ void k_diam_to_f64(DevBufs B, DevParams P, double *out) {
     out[i] = (P.precision == 0) ? ((const double *)A.diam)[i] : (double)((const float *)A.diam)[i];
 }
 
+// The other agent arrays from the caller's diameters (checked: finite,
+// positive, below 1e6 um; *bad is set when one is not) and optional arrays.
 __global__ void k_init_agents(DevBufs B, DevParams P, const double *diam_in, const double *vol_in,
-                              const uint64_t *uid_in, const uint8_t *beh_in, long long n) {
+                              const uint64_t *uid_in, const uint8_t *beh_in, long long n, int *bad) {
   const AgentSet A = *B.A;
   const double pi = 3.141592653589793;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const double d = diam_in[i];
+    if (!(isfinite(d) && d > 0.0 && d < 1e6)) atomicOr(bad, 1);
     if (P.precision == 0) ((double *)A.diam)[i] = d;
     else ((float *)A.diam)[i] = __double2float_rn(d);
     if (A.vol) A.vol[i] = vol_in ? vol_in[i] : __dmul_rn(__dmul_rn(__dmul_rn(pi / 6.0, d), d), d);
@@ -894,12 +897,20 @@ __global__ void k_init_agents(DevBufs B, DevParams P, const double *diam_in, con
   }
 }
 
-__global__ void k_validate(const double *x, const double *y, const double *z, const double *d, long long n,
-                           int *bad) {
+// The caller's positions into both position buffers (the second one: no
+// movement history yet), checked on the way (finite, within +-1e9 um); *bad
+// is set when one is not.  (sx, sy, sz) may be set 0's own first buffers, which
+// are then not written again.
+__global__ void k_positions_in(const double *sx, const double *sy, const double *sz, AgentSet A, long long n,
+                               int *bad) {
+  const bool copy0 = sx != A.x[0];
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const double a = x[i], b = y[i], c = z[i], e = d[i];
-    const bool ok = isfinite(a) && isfinite(b) && isfinite(c) && fabs(a) < 1e9 && fabs(b) < 1e9 && fabs(c) < 1e9 &&
-                    isfinite(e) && e > 0.0 && e < 1e6;
+    const double a = sx[i], b = sy[i], c = sz[i];
+    if (copy0) { A.x[0][i] = a; A.y[0][i] = b; A.z[0][i] = c; }
+    A.x[1][i] = a;
+    A.y[1][i] = b;
+    A.z[1][i] = c;
+    const bool ok = isfinite(a) && isfinite(b) && isfinite(c) && fabs(a) < 1e9 && fabs(b) < 1e9 && fabs(c) < 1e9;
     if (!ok) atomicOr(bad, 1);
   }
 }
@@ -945,11 +956,11 @@ void launch_diam_to_f64(const DevBufs &B, const DevParams &P, const LaunchCfg &c
   k_diam_to_f64<<<c.agent_blocks, 256, 0, s>>>(B, P, out);
 }
 void launch_init_agents(const DevBufs &B, const DevParams &P, const LaunchCfg &c, const double *diam_in,
-                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n,
+                        const double *vol_in, const uint64_t *uid_in, const uint8_t *beh_in, long long n, int *bad,
                         cudaStream_t s) {
-  k_init_agents<<<c.agent_blocks, 256, 0, s>>>(B, P, diam_in, vol_in, uid_in, beh_in, n);
+  k_init_agents<<<c.agent_blocks, 256, 0, s>>>(B, P, diam_in, vol_in, uid_in, beh_in, n, bad);
 }
-void launch_validate(const double *x, const double *y, const double *z, const double *d, long long n, int *bad,
-                     cudaStream_t s) {
-  k_validate<<<1216, 256, 0, s>>>(x, y, z, d, n, bad);
+void launch_positions_in(const double *x, const double *y, const double *z, const AgentSet &A, long long n, int *bad,
+                         const LaunchCfg &c, cudaStream_t s) {
+  k_positions_in<<<c.agent_blocks, 256, 0, s>>>(x, y, z, A, n, bad);
 }
