@@ -576,7 +576,10 @@ def main():
     traffic, sha = committed_traffic(agents / kp)
     peaks = measured_peaks()
     hbm = peaks.get("hbm_gbs")
-    roofline = {"bound": "alu", "kernel": "force phase of the default hybrid launch: k_force<FP32,STEP> (4 lanes per agent) on bricks of 192 agents or more, k_force_sparse on the lighter ones",
+    roofline = {"bound": "alu",
+                "kernel": "force phase of the default hybrid launch: k_force<FP32,STEP> (2 to 32 lanes per agent, "
+                          "following the agents left in a box) on bricks of 192 agents or more, k_force_sparse on "
+                          "the lighter ones",
                 "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s", "frac": achieved / peak_alu,
                 "traffic": traffic,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (nominal, derived)",
