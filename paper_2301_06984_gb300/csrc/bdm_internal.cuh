@@ -373,12 +373,13 @@ struct LaunchCfg {
 // FP32 force kernel choice (DevParams::lanes_fixed): FORCE_TILE selects the
 // tiled kernel (k_force_tile), FORCE_SPARSE the sparse kernel
 // (k_force_sparse), FORCE_HYBRID the sparse kernel for light bricks and the
-// lane-per-agent kernel (4 lanes) for the others, a positive value the
-// lane-per-agent kernel with that many lanes per agent, -1 the lane-per-agent
-// kernel with the lanes chosen per box.  The default: the hybrid launch
+// lane-per-agent kernel with 4 lanes for the others, a positive value the
+// lane-per-agent kernel with that many lanes per agent (4: adapted per pass to
+// the agents left in the box), -1 the lane-per-agent kernel with the lanes
+// chosen per box by a cost model.  The default: the hybrid launch
 #define FORCE_TILE 0
 #define FORCE_SPARSE (-3)
-#define FORCE_HYBRID (-4)  // the sparse kernel for light bricks, 4 lanes per agent for the others
+#define FORCE_HYBRID (-4)  // the sparse kernel for light bricks, the lane-per-agent kernel (4) for the others
 #define FORCE_LIGHT_MAX 192
 #define FORCE_LANES_DEFAULT FORCE_HYBRID
 

@@ -9,9 +9,11 @@
 //
 // Work decomposition: one CTA per occupied 4x4x4 brick (fetched dynamically),
 // one warp per box.  The warp resolves the 27 stencil boxes once (lanes 0..26),
-// then takes the box's agents in groups: S lanes per agent split the candidate
-// boxes (FP32 form; S chosen per box from its occupancy and candidate count)
-// and a shuffle tree reduces the S partial sums.  The FP64 form keeps one lane
+// then takes the box's agents in passes: S lanes per agent split the staged
+// candidates (FP32 form; with 4 lanes per agent, S follows the agents left in
+// the box: 2 while 11 or more are left, 4, and 8 to 32 for a last pass of 4 or
+// fewer; lanes = -1 chooses S per box by a cost model) and a shuffle tree
+// reduces the S partial sums.  The FP64 form keeps one lane
 // per agent and the canonical summation order (stencil boxes dz, dy, dx
 // ascending; ascending storage index inside a box), which makes it bit-equal
 // to the FP64 oracle.  Both forms decide "neighbour" (d^2 < R^2) and
@@ -876,7 +878,7 @@ __global__ void __launch_bounds__(FORCE_WARPS * 32, 4) k_force(DevBufs B, DevPar
               // ---- test the chunk in FP32, queue the candidates inside the band
               unsigned qlen = 0;
               if (compute) {
-                // the default stride (4 lanes per agent) with constant offsets
+                // the stride of 4 lanes per agent with constant offsets
                 qlen = (S == 4) ? scan_chunk<4>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, 4u, fill, P.R2_hi_f)
                                 : scan_chunk<0>(sc, &s_q[warp][0][lane], cq, (unsigned)sub, (unsigned)S, fill,
                                                 P.R2_hi_f);
@@ -2327,8 +2329,9 @@ void launch_force(const DevBufs &B, const DevParams &P, const LaunchCfg &c, int 
 #define LF(PR, MO, SP, TY) k_force<PR, MO, SP, TY><<<g, FORCE_WARPS * 32, 0, s>>>(B, P)
 #define LT(MO, TY) k_force_tile<MO, TY><<<g, TILE_WARPS * 32, 0, s>>>(B, P)
 #define LS(MO, TY) k_force_sparse<MO, TY><<<2 * g, SP_WARPS * 32, 0, s>>>(B, P)
-  // the hybrid launch: the lane-per-agent kernel (4 lanes) on the bricks that
-  // are not light, then the sparse kernel on the light ones
+  // the hybrid launch: the lane-per-agent kernel (4 lanes per agent, adapted
+  // per pass) on the bricks that are not light, then the sparse kernel on the
+  // light ones
   DevParams Pd = P, Pl = P;
   Pd.brick_class = 1;
   Pd.lanes_fixed = 4;
