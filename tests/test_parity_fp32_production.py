@@ -126,3 +126,39 @@ def test_fp32_edge_cases(kind):
     pos, a = H.gpu_positions(s)
     assert np.array_equal(a["uid"], o_run.uid[: o_run.n])
     H.assert_positions(pos, o_run.positions(), what="positions edge %s, 3 iterations" % kind)
+
+
+# ------------------------------------------------------- lanes per pass
+def _box_count_workload(seed=44, L=12.0):
+    # boxes of edge L = R on an 8 x 5 plane, box b holding exactly b + 1
+    # agents (1..40), plus one box of 48: every pass shape of the
+    # lane-per-agent kernel (1, 2, 3-4 agents on 32, 16, 8 lanes; 5-8 on 4;
+    # 9-10 as 8 + 1-2; 11-16 on 2 lanes; 17 or more as 16 + the rest).  The
+    # grid's box boundaries are the multiples of L, so an agent strictly
+    # inside a cell is in that box.
+    rng = np.random.default_rng(seed)
+    cells = [(10 + b % 8, 10 + b // 8, 10, b + 1) for b in range(40)] + [(20, 10, 10, 48)]
+    p, d = [], []
+    for cx, cy, cz, c in cells:
+        p.append(np.stack([rng.uniform(k * L + 0.05, (k + 1) * L - 0.05, c) for k in (cx, cy, cz)]))
+        d.append(rng.uniform(8.0, 12.0, c))
+    p = np.concatenate(p, axis=1)
+    d = np.asarray(np.concatenate(d), np.float32).astype(np.float64)
+    return W.Workload("box-counts", p[0].copy(), p[1].copy(), p[2].copy(), d,
+                      dict(R=L, L=L, dt=0.01, dmax=3.0, precision="fp32", seed=seed), steps=3)
+
+
+@pytest.mark.parametrize("lanes", [4, -4])
+def test_lane_schedule_every_pass_shape(lanes):
+    w = _box_count_workload()
+    P = H.oracle_params(w)
+    o = H.oracle_state(w)
+    f_o, nz_o, nnb_o, sc, sa = o.forces_of(P, with_scale=True, with_scale_abs=True)
+    s = H.gpu_sim(w, precision="fp32", keep_forces=True)
+    s.set_force_kernel(lanes)
+    f_g, nz_g, nnb_g = s.forces_now()
+    assert np.array_equal(nnb_g, nnb_o), "neighbour counts differ"
+    assert np.array_equal(nz_g, nz_o), "contact counts differ"
+    H.assert_fp32_forces(f_g, f_o, sa, sc, what="box counts 1-40 and 48, force-only kernel, lanes=%d" % lanes)
+    for it in range(1, 4):
+        H.production_step_vs_oracle(s, P, what="box counts iteration %d, production kernel, lanes=%d" % (it, lanes))
