@@ -938,7 +938,9 @@ void launch_scatter(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cu
 }
 void launch_brick_sort(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
   k_brick_sort_small<<<c.occ_blocks, BSW_WARPS * 32, 0, s>>>(B, P);
-  k_brick_sort<<<c.occ_blocks, BS_THREADS, 0, s>>>(B, P);
+  // the block-per-brick sort with twice the blocks of the other grid kernels:
+  // each block sorts one brick at a time, so more bricks are in flight per SM
+  k_brick_sort<<<2 * c.occ_blocks, BS_THREADS, 0, s>>>(B, P);
 }
 void launch_gather(const DevBufs &B, const DevParams &P, const LaunchCfg &c, cudaStream_t s) {
   k_gather<<<c.agent_blocks, 256, 0, s>>>(B, P);
