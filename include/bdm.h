@@ -149,12 +149,15 @@ int bdm_create(const bdm_params *params, void *stream, bdm_sim **out);
  * 1).  xyz: 3 x n doubles (x[0..n), y[0..n), z[0..n)); diam: n doubles (um;
  * rounded to float in BDM_FP32_FORCE); vol: n doubles or NULL (= pi/6 d^3);
  * uid: n or NULL (= 0..n-1); behavior: n bytes of BDM_BEH_* bits or NULL
- * (= BDM_BEH_GROW if growth_per_step > 0, plus BDM_BEH_WALK if walk_step > 0); sim_offsets: n_sims + 1 increasing offsets starting at 0 and ending at
+ * (= BDM_BEH_GROW if growth_per_step > 0, plus BDM_BEH_WALK if walk_step >
+ * 0); sim_offsets: n_sims + 1 increasing offsets starting at 0 and ending at
  * n, or NULL when n_sims == 1; step and next_uid restore the iteration counter
  * and the uid counter (checkpoint/resume).  The history of static detection
  * starts empty, so no agent is static in the first iteration after this call.
- * Errors: BDM_EINVAL (n < 0, NULL xyz/diam with n > 0, non-finite or
- * non-positive diameter, non-finite position, bad offsets), BDM_ECAPACITY
+ * The call returns when the population is set (or refused).
+ * Errors: BDM_EINVAL (n < 0, NULL xyz/diam with n > 0, a coordinate that is
+ * not finite or not within +-1e9 um, a diameter that is not finite or not in
+ * (0, 1e6) um, bad offsets; no agents are set then), BDM_ECAPACITY
  * (n > capacity), BDM_ECUDA. */
 int bdm_set_agents(bdm_sim *sim, int64_t n, const double *xyz, const double *diam, const double *vol,
                    const uint64_t *uid, const uint8_t *behavior, const int64_t *sim_offsets, int64_t step,
